@@ -1,0 +1,186 @@
+/*
+ * eap.h -- C ABI of libeap: batched elastic-distance 1-NN search and distance
+ * matrices with EAPruned (pruning + early abandoning) on one GB300 GPU.
+ *
+ * Method: Herrmann & Webb, "Early Abandoning and Pruning for Elastic
+ * Distances including Dynamic Time Warping" (arXiv 2102.05221).
+ *
+ * Conventions for every entry point
+ *   - Return value: EAP_OK (0) or a negative EAP_E* code; eap_strerror()
+ *     names it.  No C++ exception ever crosses this boundary.
+ *   - Ownership: the caller owns every buffer it passes in and keeps it alive
+ *     until the call's work on the stream has finished.  The library owns only
+ *     its own scratch (stream-ordered device allocations released on the same
+ *     stream) and eap_server objects.
+ *   - Memory spaces: pointers documented "device" must be CUDA device (or
+ *     managed) memory of the current device; "host" pointers are ordinary host
+ *     memory.  eap_nn1_host() is the one entry point that takes host buffers
+ *     for everything.
+ *   - Asynchrony: device-pointer entry points enqueue work on `cuda_stream`
+ *     (a cudaStream_t; NULL = the legacy default stream) and return without
+ *     waiting, unless `opt_stats` is non-NULL, in which case they synchronise
+ *     the stream to fill it.
+ *   - Series sets: a concatenated float32 buffer plus int64 element offsets
+ *     and int32 lengths (one per series), given both on the device (read by
+ *     the kernels) and on the host (read by the scheduler, never written).
+ *   - Numerics: the kernels compute in float32; +inf is the "abandoned / no
+ *     alignment" value.  Inputs must be finite.
+ */
+#ifndef EAP_H
+#define EAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define EAP_OK          0
+#define EAP_EINVAL     (-1)  /* invalid argument (null pointer, length <= 0, bad parameter, size mismatch) */
+#define EAP_ENOMEM     (-2)  /* device or host allocation failed */
+#define EAP_EAGAIN     (-3)  /* serving: not admitted now / result not ready yet */
+#define EAP_ETIMEOUT   (-4)  /* a bounded device wait or a serving deadline expired */
+#define EAP_EDEVICE    (-5)  /* a CUDA call failed (no device, launch failure, ...) */
+#define EAP_EINTERNAL  (-6)  /* an internal consistency check failed */
+
+/* ---- distances (Section 2.3 of the paper) -------------------------------
+ * EAP_DTW   Eq. DTW: cost(s_i,t_j) + min of the three dependencies, +inf borders.
+ * EAP_CDTW  DTW restricted to the Sakoe-Chiba window |i-j| <= w (Section 2.3.2).
+ * EAP_WDTW  Eq. WDTW: cell cost weighted by wmax/(1+exp(-g(|i-j| - L/2))), L = max length.
+ * EAP_ERP   Eq. ERP: gap value g, computed borders, window w.
+ * EAP_MSM   Eq. MSM with the split/merge cost Eq. MSMCost (penalty c).
+ * EAP_TWE   Eq. TWE with Eq. TWECost (stiffness nu, penalty lambda, timestamps tau_i = i). */
+typedef enum { EAP_DTW = 0, EAP_CDTW = 1, EAP_WDTW = 2, EAP_ERP = 3, EAP_MSM = 4, EAP_TWE = 5 } eap_kind;
+
+/* Point cost "cost(a,b)" of Section 2.3.  EAP_COST_DEFAULT picks squared
+ * for DTW/CDTW/WDTW and absolute for ERP/TWE; MSM always uses |a-b|. */
+typedef enum { EAP_COST_DEFAULT = -1, EAP_COST_SQ = 0, EAP_COST_ABS = 1 } eap_cost;
+
+/* Optional lower-bound cascade ahead of the DP (Alg. 2; LB_Keogh of
+ * Section 4.2).  Only for DTW/CDTW with equal-length series; ignored otherwise. */
+typedef enum { EAP_LB_NONE = 0, EAP_LB_KEOGH = 1, EAP_LB_KEOGH2 = 2 } eap_lb;
+
+typedef struct {
+    int32_t kind;          /* eap_kind */
+    int32_t cost;          /* eap_cost */
+    float   window_ratio;  /* CDTW/ERP: w = floor(ratio * max(L_S, L_T)) when window < 0; < 0 = no window */
+    int32_t window;        /* CDTW/ERP: absolute window w >= 0; < 0 = use window_ratio */
+    float   wdtw_g;        /* WDTW g >= 0 */
+    float   wdtw_wmax;     /* WDTW weight scale wmax > 0 (the paper's form has wmax = 1) */
+    float   erp_gap;       /* ERP gap value g (any finite value) */
+    float   msm_c;         /* MSM penalty c >= 0 */
+    float   twe_nu;        /* TWE stiffness nu >= 0 */
+    float   twe_lambda;    /* TWE penalty lambda >= 0 */
+    int32_t lb;            /* eap_lb */
+    int32_t prune;         /* 1 = EAPruned (Alg. 5 semantics); 0 = Base (Alg. 3: no pruning, no abandoning) */
+} eap_params;
+
+/* Fills *p with the defaults of the distance: window ratio 0.1 for CDTW/ERP,
+ * g = 0.05 and wmax = 1 for WDTW, gap 0 for ERP, c = 0.5 for MSM,
+ * nu = 0.001 and lambda = 1 for TWE, default cost, no LB, prune = 1. */
+void eap_params_default(eap_params* p, int32_t kind);
+
+typedef struct {
+    const float*   data;       /* device: all series back to back (float32) */
+    const int64_t* offsets;    /* device: element offset of series k in data */
+    const int32_t* lengths;    /* device: length of series k (>= 1) */
+    const int64_t* h_offsets;  /* host mirror of offsets */
+    const int32_t* h_lengths;  /* host mirror of lengths */
+    int64_t        data_len;   /* number of floats in data (bounds check) */
+    int32_t        count;      /* number of series (>= 0) */
+    int32_t        reserved_;
+} eap_series_set;
+
+/* Work counters of one call (filled when a non-NULL pointer is passed). */
+typedef struct {
+    uint64_t pairs;            /* (query, candidate) or (i, j) pairs given to the DP */
+    uint64_t pairs_lb_pruned;  /* pairs skipped because their lower bound exceeded the cut-off */
+    uint64_t pairs_abandoned;  /* pairs the DP early-abandoned (returned +inf) */
+    uint64_t cells_effective;  /* sum over all pairs of L_S * L_T */
+    uint64_t cells_computed;   /* cells the DP kernels evaluated (after pruning) */
+} eap_stats;
+
+/* ---- entry points -------------------------------------------------------- */
+
+/* 1-NN search (Alg. 1, each distance evaluation Alg. 5 with the query's
+ * current best-so-far as cut-off).  For every query q, finds the candidate c
+ * minimising D(Q_q, C_c); ties go to the lowest candidate index; D values
+ * that are +inf (infeasible window) never win.
+ *   queries, refs : series sets (device + host mirrors).
+ *   out_idx       : device int32[queries->count]; -1 when no candidate is finite.
+ *   out_dist      : device float[queries->count]; +inf when none.
+ * The cut-off starts at the smallest diagonal-path cost of the query over all
+ * candidates (a valid upper bound, Section 3 intro), candidates are evaluated
+ * nearest-diagonal-cost first, and concurrent candidates of one query share
+ * the cut-off through a packed 64-bit atomicMin. */
+int eap_nn1(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs,
+            int32_t* out_idx, float* out_dist, void* cuda_stream, eap_stats* opt_stats);
+
+/* The same search with every buffer in host memory: copies the sets to the
+ * device, runs eap_nn1 on an internal stream, copies the results back and
+ * waits.  q_data/r_data: host float32; offsets/lengths: host; out_*: host. */
+int eap_nn1_host(const eap_params* p,
+                 const float* q_data, const int64_t* q_offsets, const int32_t* q_lengths, int32_t nq,
+                 const float* r_data, const int64_t* r_offsets, const int32_t* r_lengths, int32_t nr,
+                 int32_t* out_idx, float* out_dist, eap_stats* opt_stats);
+
+#define EAP_PRUNE_ONLY 0   /* EAPruned with each pair's own diagonal-path cost as cut-off: exact, prunes but never abandons (Section 3 intro) */
+#define EAP_BASE       1   /* plain Base DP (Alg. 3) */
+
+/* All-pairs distance matrix of one set: out_matrix is device float
+ * [count * count], row-major, symmetric, zero diagonal.  Each unordered pair
+ * is computed once (D(set_i, set_j) with i < j, set_i on the rows). */
+int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode,
+                 void* cuda_stream, eap_stats* opt_stats);
+
+/* Raw EAPruned on an explicit list of n pairs: out[k] = D(A_ia[k], B_ib[k])
+ * if it is <= cutoff[k], else +inf (Section 2.2: an early-abandoned
+ * distance signals abandoning by returning +inf).  ia, ib, cutoff, out are
+ * device arrays of n elements.  With p->prune = 0 the cut-off is ignored and
+ * the plain D is returned. */
+int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
+              const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
+              void* cuda_stream, eap_stats* opt_stats);
+
+/* LB_Keogh(A_ia[k], B_ib[k]) for n pairs of equal length (textbook form,
+ * Section 4.2): the envelope of A_ia[k] with window w = floor(ratio * L) (or
+ * the absolute window) bounds the points of B_ib[k].  Squared or absolute
+ * cost as the parameters say.  out: device float[n]; pairs whose lengths
+ * differ get 0 (no bound). */
+int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
+                 const int32_t* ia, const int32_t* ib, float* out, int32_t n, void* cuda_stream);
+
+/* ---- serving ------------------------------------------------------------- */
+typedef struct eap_server eap_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;   /* admission budget for resident sets + in-flight queries (0 = 1/2 of free HBM) */
+    int32_t max_inflight;       /* queries in flight at once (0 = 4096) */
+    int32_t max_query_len;      /* longest admissible query (0 = 8192) */
+    int32_t device;             /* CUDA device ordinal */
+    int32_t reserved_;
+} eap_serve_config;
+
+eap_server* eap_serve_create(const eap_serve_config* cfg, int* status);
+/* Copies a host reference set into HBM and keeps it resident; *set_id names it. */
+int eap_serve_add_refset(eap_server* s, const float* h_data, const int64_t* h_offsets,
+                         const int32_t* h_lengths, int32_t count, int32_t* set_id);
+/* Enqueues one 1-NN query (host buffer, copied) against a resident set.
+ * EAP_EAGAIN when the query cannot be admitted now (slots or HBM budget). */
+int eap_serve_submit(eap_server* s, int32_t set_id, const eap_params* p, const float* h_query,
+                     int32_t len, uint64_t* ticket);
+/* EAP_OK with the result once the query is done, EAP_EAGAIN before. */
+int eap_serve_poll(eap_server* s, uint64_t ticket, int32_t* idx, float* dist);
+/* Blocks until every submitted query is done (bounded by timeout_ms; EAP_ETIMEOUT). */
+int eap_serve_drain(eap_server* s, int32_t timeout_ms);
+int eap_serve_destroy(eap_server* s);
+
+const char* eap_strerror(int code);
+int32_t eap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EAP_H */

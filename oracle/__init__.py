@@ -86,6 +86,9 @@ def _load():
                                     f32p, i64p, i32p, ctypes.c_int, i32p, f64p, ctypes.c_int]
             lib.orc_pairwise.restype = ctypes.c_int
             lib.orc_pairwise.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int, f64p, ctypes.c_int]
+            lib.orc_cross.restype = ctypes.c_int
+            lib.orc_cross.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int,
+                                      f32p, i64p, i32p, ctypes.c_int, f64p, ctypes.c_int]
             lib.orc_envelope.restype = None
             lib.orc_envelope.argtypes = [f32p, ctypes.c_int, ctypes.c_long, f64p, f64p]
             lib.orc_lb_keogh.restype = ctypes.c_double
@@ -148,6 +151,18 @@ def pairwise(params: OrcParams, series, nthreads: int | None = None) -> np.ndarr
     nt = nthreads or os.cpu_count() or 1
     _load().orc_pairwise(ctypes.byref(params), _ptr(d, ctypes.c_float), _ptr(o, ctypes.c_int64),
                          _ptr(l, ctypes.c_int32), n, _ptr(out, ctypes.c_double), int(nt))
+    return out
+
+
+def cross(params: OrcParams, a, b, nthreads: int | None = None) -> np.ndarray:
+    """Matrix of D(a_i, b_j) for packed sets a (rows) and b (columns), FP64."""
+    ad, ao, al = _packed_args(a)
+    bd, bo, bl = _packed_args(b)
+    out = np.zeros((len(al), len(bl)), dtype=np.float64)
+    nt = nthreads or os.cpu_count() or 1
+    _load().orc_cross(ctypes.byref(params), _ptr(ad, ctypes.c_float), _ptr(ao, ctypes.c_int64),
+                      _ptr(al, ctypes.c_int32), len(al), _ptr(bd, ctypes.c_float), _ptr(bo, ctypes.c_int64),
+                      _ptr(bl, ctypes.c_int32), len(bl), _ptr(out, ctypes.c_double), int(nt))
     return out
 
 

@@ -433,4 +433,42 @@ double orc_lb_keogh(const float* q, const float* c, int L, long w, int cost) {
     return lb;
 }
 
+
+/* ------------------------------------------------------------------------
+ * Cross matrix D(A_a, B_b) for every a, b (rows a), threads split the rows.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_params* p;
+    const float* ad; const int64_t* ao; const int32_t* al;
+    const float* bd; const int64_t* bo; const int32_t* bl;
+    int nb; double* out; int a_begin, a_end;
+} o_cross_job;
+
+static void* o_cross_worker(void* arg) {
+    o_cross_job* jb = (o_cross_job*)arg;
+    for (int a = jb->a_begin; a < jb->a_end; a++)
+        for (int b = 0; b < jb->nb; b++)
+            jb->out[(size_t)a * jb->nb + b] =
+                orc_distance(jb->p, jb->ad + jb->ao[a], jb->al[a], jb->bd + jb->bo[b], jb->bl[b]);
+    return NULL;
+}
+
+int orc_cross(const orc_params* p,
+              const float* ad, const int64_t* ao, const int32_t* al, int na,
+              const float* bd, const int64_t* bo, const int32_t* bl, int nb,
+              double* out, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > na) nthreads = na > 0 ? na : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    o_cross_job* jobs = (o_cross_job*)malloc(sizeof(o_cross_job) * (size_t)nthreads);
+    for (int k = 0; k < nthreads; k++) {
+        jobs[k] = (o_cross_job){p, ad, ao, al, bd, bo, bl, nb, out,
+                                (int)((long)na * k / nthreads), (int)((long)na * (k + 1) / nthreads)};
+        pthread_create(&th[k], NULL, o_cross_worker, &jobs[k]);
+    }
+    for (int k = 0; k < nthreads; k++) pthread_join(th[k], NULL);
+    free(th); free(jobs);
+    return 0;
+}
+
 int orc_abi_version(void) { return 1; }

@@ -1,0 +1,684 @@
+// eap_api.cu -- the C ABI of libeap (declared in include/eap.h): argument
+// validation, stream-ordered scratch, and the launch sequence of each entry
+// point, plus the small kernels that do not depend on the distance.
+//
+// 1-NN (Alg. 1 with Alg. 5 as the distance) runs as
+//   init best-so-far  ->  [ERP borders | WDTW weights]  ->  diagonal upper
+//   bounds (every query x candidate)  ->  per-query sort of the candidates by
+//   that bound + cut-off seed  ->  persistent DP over (rank, query) items  ->
+//   unpack of the packed best-so-far into (index, distance).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/eap.h"
+#include "eap_internal.h"
+
+using namespace eapd;
+
+namespace {
+
+constexpr int kMaxSeriesLen = 8192;   // longest series a call accepts (shared-memory column of the DP)
+
+// ---------------------------------------------------------------------------
+// Distance-independent kernels.
+// ---------------------------------------------------------------------------
+__global__ void init_best_kernel(unsigned long long* best, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        best[i] = pack_best(EAP_FINF, kNoIndex);
+}
+
+// One block per query: sorts that query's candidates by their diagonal-path
+// cost (bitonic sort of packed (bound bits, index) keys in shared memory, in
+// chunks of `chunk` candidates), writes the evaluation order, and seeds the
+// query's cut-off with the smallest bound (no index: any real D <= bound wins).
+__global__ void sort_seed_kernel(const float* __restrict__ ub, int nb, int chunk, int32_t* __restrict__ order,
+                                 unsigned long long* __restrict__ best) {
+    extern __shared__ unsigned long long keys[];
+    const int q = blockIdx.x;
+    const float* u = ub + (size_t)q * nb;
+    int32_t* o = order + (size_t)q * nb;
+    unsigned long long gmin = ~0ULL;
+    for (int base = 0; base < nb; base += chunk) {
+        const int cnt = min(chunk, nb - base);
+        for (int i = threadIdx.x; i < chunk; i += blockDim.x)
+            keys[i] = i < cnt ? pack_best(u[base + i], (unsigned)(base + i)) : ~0ULL;
+        __syncthreads();
+        for (int k = 2; k <= chunk; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < chunk; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long a = keys[i], b = keys[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) { keys[i] = b; keys[l] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) o[base + i] = (int32_t)(keys[i] & 0xffffffffu);
+        if (keys[0] < gmin) gmin = keys[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned bits = (unsigned)(gmin >> 32);
+        best[q] = ((unsigned long long)bits << 32) | kNoIndex;
+    }
+}
+
+__global__ void unpack_kernel(const unsigned long long* __restrict__ best, int n, int32_t* __restrict__ idx,
+                              float* __restrict__ dist, unsigned long long* stats) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long b = best[i];
+        const unsigned ix = (unsigned)(b & 0xffffffffu);
+        const float d = __uint_as_float((unsigned)(b >> 32));
+        if (ix == kNoIndex) {
+            idx[i] = -1;
+            dist[i] = EAP_FINF;
+            // A finite seed left in place means no candidate met its own bound.
+            if (d != EAP_FINF && stats) atomicAdd(stats + kStatErrors, 1ULL);
+        } else {
+            idx[i] = (int32_t)ix;
+            dist[i] = d;
+        }
+    }
+}
+
+// ERP borders (Eq. ERP): border[off + k] = sum_{m <= k+1} cost(x_m, g), in order.
+__global__ void erp_border_kernel(const float* __restrict__ data, const int64_t* __restrict__ off,
+                                  const int32_t* __restrict__ len, int n, float g, int cost,
+                                  float* __restrict__ border) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const float* x = data + off[s];
+        float* b = border + off[s];
+        float acc = 0.f;
+        const int L = len[s];
+        for (int k = 0; k < L; ++k) {
+            const float c = cost == 0 ? pcost<0>(x[k], g) : pcost<1>(x[k], g);
+            acc = __fadd_rn(acc, c);
+            b[k] = acc;
+        }
+    }
+}
+
+// Universal WDTW weight table (Eq. WDTW): entry kWdtwOff + u holds
+// wmax / (1 + exp(-g u / 2)), u = 2d - L, evaluated in double and rounded.
+__global__ void wdtw_table_kernel(float* tab, double g, double wmax) {
+    const int n = 2 * kWdtwOff + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double u = (double)(i - kWdtwOff);
+        tab[i] = (float)(wmax / (1.0 + exp(-g * (u / 2.0))));
+    }
+}
+
+__global__ void diag_zero_kernel(float* m, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m[(size_t)i * n + i] = 0.f;
+}
+
+__global__ void fill_nn_empty_kernel(int32_t* idx, float* dist, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        idx[i] = -1;
+        dist[i] = EAP_FINF;
+    }
+}
+
+// LB_Keogh for explicit pairs (textbook form): envelope of A over
+// |k - i| <= w, bound on the points of B.  One warp per pair.
+__global__ void lb_keogh_pairs_kernel(const SeriesDev A, const SeriesDev B, const int32_t* __restrict__ ia,
+                                      const int32_t* __restrict__ ib, int n, KParams kp, int cost,
+                                      float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+        const int a = ia[k], b = ib[k];
+        const int L = A.len[a];
+        float acc = 0.f;
+        if (B.len[b] == L) {
+            const float* x = A.data + A.off[a];
+            const float* y = B.data + B.off[b];
+            const int w = pair_window(kp, L, L);
+            for (int i = lane; i < L; i += 32) {
+                float U = -EAP_FINF, Lo = EAP_FINF;
+                const int k0 = max(0, i - w), k1 = min(L - 1, i + w);
+                for (int j = k0; j <= k1; ++j) {
+                    const float v = __ldg(x + j);
+                    U = fmaxf(U, v);
+                    Lo = fminf(Lo, v);
+                }
+                const float c = __ldg(y + i);
+                float e = 0.f;
+                if (c > U) e = cost == 0 ? pcost<0>(c, U) : pcost<1>(c, U);
+                else if (c < Lo) e = cost == 0 ? pcost<0>(c, Lo) : pcost<1>(c, Lo);
+                acc = __fadd_rn(acc, e);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(EAP_FULL, acc, o));
+        }
+        if (lane == 0) out[k] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers.
+// ---------------------------------------------------------------------------
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    return sms;
+}
+
+int resolve_cost(const eap_params* p) {
+    if (p->kind == EAP_MSM) return 1;
+    if (p->cost == EAP_COST_SQ || p->cost == EAP_COST_ABS) return p->cost;
+    return (p->kind == EAP_ERP || p->kind == EAP_TWE) ? 1 : 0;
+}
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+int validate_params(const eap_params* p) {
+    if (!p) return EAP_EINVAL;
+    if (p->kind < EAP_DTW || p->kind > EAP_TWE) return EAP_EINVAL;
+    if (p->cost != EAP_COST_DEFAULT && p->cost != EAP_COST_SQ && p->cost != EAP_COST_ABS) return EAP_EINVAL;
+    if (p->prune != 0 && p->prune != 1) return EAP_EINVAL;
+    if (p->lb < EAP_LB_NONE || p->lb > EAP_LB_KEOGH2) return EAP_EINVAL;
+    if (!finite_f(p->window_ratio)) return EAP_EINVAL;
+    if (p->kind == EAP_WDTW && !(finite_f(p->wdtw_g) && p->wdtw_g >= 0.f && finite_f(p->wdtw_wmax) && p->wdtw_wmax > 0.f))
+        return EAP_EINVAL;
+    if (p->kind == EAP_ERP && !finite_f(p->erp_gap)) return EAP_EINVAL;
+    if (p->kind == EAP_MSM && !(finite_f(p->msm_c) && p->msm_c >= 0.f)) return EAP_EINVAL;
+    if (p->kind == EAP_TWE && !(finite_f(p->twe_nu) && p->twe_nu >= 0.f && finite_f(p->twe_lambda) && p->twe_lambda >= 0.f))
+        return EAP_EINVAL;
+    return EAP_OK;
+}
+
+int validate_set(const eap_series_set* s, int* max_len) {
+    if (!s || s->count < 0) return EAP_EINVAL;
+    int mx = 0;
+    if (s->count == 0) { *max_len = 0; return EAP_OK; }
+    if (!s->data || !s->offsets || !s->lengths || !s->h_offsets || !s->h_lengths) return EAP_EINVAL;
+    for (int i = 0; i < s->count; ++i) {
+        const int32_t L = s->h_lengths[i];
+        const int64_t o = s->h_offsets[i];
+        if (L <= 0 || L > kMaxSeriesLen || o < 0 || o + L > s->data_len) return EAP_EINVAL;
+        if (L > mx) mx = L;
+    }
+    *max_len = mx;
+    return EAP_OK;
+}
+
+KParams make_kparams(const eap_params* p) {
+    KParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.wdtw_g = p->wdtw_g;
+    kp.wdtw_wmax = p->wdtw_wmax;
+    kp.erp_gap = p->erp_gap;
+    kp.msm_c = p->msm_c;
+    kp.twe_nu = p->twe_nu;
+    kp.twe_nu2 = 2.0f * p->twe_nu;
+    kp.twe_lambda = p->twe_lambda;
+    kp.windowed = (p->kind == EAP_CDTW || p->kind == EAP_ERP) ? 1 : 0;
+    kp.window_abs = p->window;
+    kp.window_ratio = p->window_ratio;
+    return kp;
+}
+
+// Strip width per lane: 32*W columns per panel.  EAP_W overrides (tuning).
+int choose_w(int max_cols, int prune) {
+    const char* e = std::getenv("EAP_W");
+    if (e) {
+        const int w = std::atoi(e);
+        if (w == 4 || w == 8 || w == 16) return w;
+    }
+    if (max_cols <= 128) return 4;
+    if (!prune && max_cols > 256) return 16;
+    return 8;
+}
+
+int dispatch(const eaph::LaunchCtx& c, bool ub_only) {
+    switch (c.kind) {
+        case EAP_DTW: return eaph::launch_dp_dtw(c, ub_only);
+        case EAP_CDTW: return eaph::launch_dp_cdtw(c, ub_only);
+        case EAP_WDTW: return eaph::launch_dp_wdtw(c, ub_only);
+        case EAP_ERP: return eaph::launch_dp_erp(c, ub_only);
+        case EAP_MSM: return eaph::launch_dp_msm(c, ub_only);
+        case EAP_TWE: return eaph::launch_dp_twe(c, ub_only);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+// One stream-ordered scratch block carved into aligned pieces.
+struct Scratch {
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    cudaStream_t st = nullptr;
+    int err = 0;
+    void* take(size_t bytes) {
+        const size_t a = (used + 255) & ~(size_t)255;
+        used = a + bytes;
+        return base ? base + a : nullptr;
+    }
+    int alloc(cudaStream_t s) {
+        st = s;
+        size = used;
+        used = 0;
+        if (size == 0) return EAP_OK;
+        if (cudaMallocAsync((void**)&base, size, s) != cudaSuccess) { cudaGetLastError(); base = nullptr; return EAP_ENOMEM; }
+        return EAP_OK;
+    }
+    void release() {
+        if (base) cudaFreeAsync(base, st);
+        base = nullptr;
+    }
+};
+
+SeriesDev dev_set(const eap_series_set* s, const float* border) {
+    return SeriesDev{s->data, s->offsets, s->lengths, border, s->count};
+}
+
+unsigned long long sum_cells(const eap_series_set* a, const eap_series_set* b) {
+    unsigned long long sa = 0, sb = 0;
+    for (int i = 0; i < a->count; ++i) sa += (unsigned long long)a->h_lengths[i];
+    for (int i = 0; i < b->count; ++i) sb += (unsigned long long)b->h_lengths[i];
+    return sa * sb;
+}
+
+int cuda_status(int e) { return e == 0 ? EAP_OK : EAP_EDEVICE; }
+
+// Shared body of 1-NN for device-resident sets.
+int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
+             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int mq = 0, mr = 0;
+    if ((rc = validate_set(qs, &mq)) || (rc = validate_set(rs, &mr))) return rc;
+    if (qs->count > 0 && (!out_idx || !out_dist)) return EAP_EINVAL;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    const int nq = qs->count, nr = rs->count;
+    if (nq == 0) return EAP_OK;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    if (nr == 0) {
+        fill_nn_empty_kernel<<<(nq + 255) / 256, 256, 0, st>>>(out_idx, out_dist, nq);
+        return cuda_status((int)cudaGetLastError());
+    }
+    const bool prune = p->prune != 0;
+    const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
+    const int cost = resolve_cost(p);
+    const unsigned long long items = (unsigned long long)nq * nr;
+
+    Scratch sc;
+    auto layout = [&]() {
+        struct { unsigned long long *best, *ctr, *stats; float* ub; int32_t* order; float *bq, *br, *wt; } L;
+        L.best = (unsigned long long*)sc.take(sizeof(unsigned long long) * nq);
+        L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
+        L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
+        L.ub = prune ? (float*)sc.take(sizeof(float) * items) : nullptr;
+        L.order = prune ? (int32_t*)sc.take(sizeof(int32_t) * items) : nullptr;
+        L.bq = erp ? (float*)sc.take(sizeof(float) * (size_t)qs->data_len) : nullptr;
+        L.br = erp ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
+        L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        return L;
+    };
+    layout();
+    if ((rc = sc.alloc(st))) return rc;
+    const auto L = layout();
+    unsigned long long* d_best = L.best;
+    unsigned long long* d_ctr = L.ctr;
+    unsigned long long* d_stats = L.stats;
+    float* d_ub = L.ub;
+    int32_t* d_order = L.order;
+    float* d_bq = L.bq;
+    float* d_br = L.br;
+    float* d_wt = L.wt;
+
+    int e = 0;
+    e |= (int)cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
+    e |= (int)cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * kStatCount, st);
+    init_best_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq);
+    if (erp) {
+        erp_border_kernel<<<(nq + 127) / 128, 128, 0, st>>>(qs->data, qs->offsets, qs->lengths, nq, p->erp_gap, cost, d_bq);
+        erp_border_kernel<<<(nr + 127) / 128, 128, 0, st>>>(rs->data, rs->offsets, rs->lengths, nr, p->erp_gap, cost, d_br);
+    }
+    if (wdtw) wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(d_wt, (double)p->wdtw_g, (double)p->wdtw_wmax);
+    e |= (int)cudaGetLastError();
+    if (e) { sc.release(); return EAP_EDEVICE; }
+
+    eaph::LaunchCtx c;
+    std::memset(&c, 0, sizeof(c));
+    c.job.mode = kModeNN1;
+    c.job.A = dev_set(qs, d_bq);
+    c.job.B = dev_set(rs, d_br);
+    c.job.nitems = items;
+    c.job.counter = d_ctr;
+    c.job.order = d_order;
+    c.job.best = d_best;
+    c.job.stats = d_stats;
+    c.job.wdtw_table = d_wt;
+    c.job.bnd_stride = ((mq + 1) + 31) & ~31;
+    c.kp = make_kparams(p);
+    c.kp.wdtw_w = d_wt;
+    c.kind = p->kind;
+    c.cost = cost;
+    c.prune = prune ? 1 : 0;
+    c.W = choose_w(mr, c.prune);
+    c.sms = sms;
+    c.max_rows = mq;
+    c.stream = st;
+    c.ub = d_ub;
+    if (prune) {
+        if ((e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
+        int chunk = 1;
+        while (chunk < nr && chunk < 4096) chunk <<= 1;
+        sort_seed_kernel<<<nq, 512, sizeof(unsigned long long) * chunk, st>>>(d_ub, nr, chunk, d_order, d_best);
+        if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
+    }
+    if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+    unpack_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq, out_idx, out_dist, d_stats);
+    if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
+    unsigned long long h[kStatCount];
+    if (stats || dev_stats_keep) {
+        if (cudaMemcpyAsync(h, d_stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) { sc.release(); return EAP_EDEVICE; }
+    }
+    sc.release();
+    if (stats || dev_stats_keep) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return EAP_EDEVICE;
+        if (stats) {
+            stats->pairs = h[kStatPairs] + h[kStatLbPruned];
+            stats->pairs_lb_pruned = h[kStatLbPruned];
+            stats->pairs_abandoned = h[kStatAbandoned];
+            stats->cells_computed = h[kStatCells];
+            stats->cells_effective = sum_cells(qs, rs);
+        }
+        if (dev_stats_keep) std::memcpy(dev_stats_keep, h, sizeof(h));
+        if (h[kStatErrors]) return EAP_EINTERNAL;
+    }
+    return EAP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void eap_params_default(eap_params* p, int32_t kind) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->kind = kind;
+    p->cost = EAP_COST_DEFAULT;
+    p->window_ratio = (kind == EAP_CDTW || kind == EAP_ERP) ? 0.1f : -1.0f;
+    p->window = -1;
+    p->wdtw_g = 0.05f;
+    p->wdtw_wmax = 1.0f;
+    p->erp_gap = 0.0f;
+    p->msm_c = 0.5f;
+    p->twe_nu = 0.001f;
+    p->twe_lambda = 1.0f;
+    p->lb = EAP_LB_NONE;
+    p->prune = 1;
+}
+
+const char* eap_strerror(int code) {
+    switch (code) {
+        case EAP_OK: return "ok";
+        case EAP_EINVAL: return "invalid argument";
+        case EAP_ENOMEM: return "out of memory";
+        case EAP_EAGAIN: return "try again (not admitted / not ready)";
+        case EAP_ETIMEOUT: return "timed out";
+        case EAP_EDEVICE: return "CUDA device error";
+        case EAP_EINTERNAL: return "internal consistency check failed";
+    }
+    return "unknown error";
+}
+
+int32_t eap_version(void) { return 1; }
+
+int eap_nn1(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t* out_idx,
+            float* out_dist, void* cuda_stream, eap_stats* opt_stats) {
+    return nn1_impl(p, queries, refs, out_idx, out_dist, (cudaStream_t)cuda_stream, opt_stats, nullptr);
+}
+
+int eap_nn1_host(const eap_params* p, const float* q_data, const int64_t* q_offsets, const int32_t* q_lengths,
+                 int32_t nq, const float* r_data, const int64_t* r_offsets, const int32_t* r_lengths, int32_t nr,
+                 int32_t* out_idx, float* out_dist, eap_stats* opt_stats) {
+    if (nq < 0 || nr < 0) return EAP_EINVAL;
+    if (nq > 0 && (!q_data || !q_offsets || !q_lengths || !out_idx || !out_dist)) return EAP_EINVAL;
+    if (nr > 0 && (!r_data || !r_offsets || !r_lengths)) return EAP_EINVAL;
+    int64_t qlen = 0, rlen = 0;
+    for (int i = 0; i < nq; ++i) qlen = std::max<int64_t>(qlen, q_offsets[i] + std::max(0, q_lengths[i]));
+    for (int i = 0; i < nr; ++i) rlen = std::max<int64_t>(rlen, r_offsets[i] + std::max(0, r_lengths[i]));
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return EAP_EDEVICE;
+    const size_t bytes = sizeof(float) * (size_t)(qlen + rlen) + (sizeof(int64_t) + sizeof(int32_t)) * (size_t)(nq + nr)
+                         + (sizeof(int32_t) + sizeof(float)) * (size_t)nq + 6 * 256;
+    char* d = nullptr;
+    if (cudaMallocAsync((void**)&d, bytes, st) != cudaSuccess) { cudaGetLastError(); cudaStreamDestroy(st); return EAP_ENOMEM; }
+    size_t used = 0;
+    auto take = [&](size_t b) { const size_t a = (used + 255) & ~(size_t)255; used = a + b; return d + a; };
+    float* dq = (float*)take(sizeof(float) * qlen);
+    float* dr = (float*)take(sizeof(float) * rlen);
+    int64_t* dqo = (int64_t*)take(sizeof(int64_t) * nq);
+    int32_t* dql = (int32_t*)take(sizeof(int32_t) * nq);
+    int64_t* dro = (int64_t*)take(sizeof(int64_t) * nr);
+    int32_t* drl = (int32_t*)take(sizeof(int32_t) * nr);
+    int32_t* didx = (int32_t*)take(sizeof(int32_t) * nq);
+    float* ddist = (float*)take(sizeof(float) * nq);
+    int e = 0;
+    if (qlen) e |= (int)cudaMemcpyAsync(dq, q_data, sizeof(float) * qlen, cudaMemcpyHostToDevice, st);
+    if (rlen) e |= (int)cudaMemcpyAsync(dr, r_data, sizeof(float) * rlen, cudaMemcpyHostToDevice, st);
+    if (nq) {
+        e |= (int)cudaMemcpyAsync(dqo, q_offsets, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st);
+        e |= (int)cudaMemcpyAsync(dql, q_lengths, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st);
+    }
+    if (nr) {
+        e |= (int)cudaMemcpyAsync(dro, r_offsets, sizeof(int64_t) * nr, cudaMemcpyHostToDevice, st);
+        e |= (int)cudaMemcpyAsync(drl, r_lengths, sizeof(int32_t) * nr, cudaMemcpyHostToDevice, st);
+    }
+    int rc = e ? EAP_EDEVICE : EAP_OK;
+    if (rc == EAP_OK) {
+        eap_series_set qs{dq, dqo, dql, q_offsets, q_lengths, qlen, nq, 0};
+        eap_series_set rs{dr, dro, drl, r_offsets, r_lengths, rlen, nr, 0};
+        rc = nn1_impl(p, &qs, &rs, didx, ddist, st, opt_stats, nullptr);
+    }
+    if (rc == EAP_OK && nq) {
+        e = (int)cudaMemcpyAsync(out_idx, didx, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st);
+        e |= (int)cudaMemcpyAsync(out_dist, ddist, sizeof(float) * nq, cudaMemcpyDeviceToHost, st);
+        if (e) rc = EAP_EDEVICE;
+    }
+    cudaFreeAsync(d, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == EAP_OK) rc = EAP_EDEVICE;
+    cudaStreamDestroy(st);
+    return rc;
+}
+
+int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode, void* cuda_stream,
+                 eap_stats* opt_stats) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int mx = 0;
+    if ((rc = validate_set(set, &mx))) return rc;
+    if (mode != EAP_PRUNE_ONLY && mode != EAP_BASE) return EAP_EINVAL;
+    if (set->count > 0 && !out_matrix) return EAP_EINVAL;
+    if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
+    const int n = set->count;
+    if (n == 0) return EAP_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    const bool prune = mode == EAP_PRUNE_ONLY;
+    const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
+    const int cost = resolve_cost(p);
+    const unsigned long long items = (unsigned long long)n * (n - 1) / 2;
+
+    Scratch sc;
+    auto layout = [&]() {
+        struct { unsigned long long *ctr, *stats; float *ub, *bs, *wt; } L;
+        L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
+        L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
+        L.ub = prune ? (float*)sc.take(sizeof(float) * (items ? items : 1)) : nullptr;
+        L.bs = erp ? (float*)sc.take(sizeof(float) * (size_t)set->data_len) : nullptr;
+        L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        return L;
+    };
+    layout();
+    if ((rc = sc.alloc(st))) return rc;
+    auto L = layout();
+    int e = 0;
+    e |= (int)cudaMemsetAsync(L.ctr, 0, sizeof(unsigned long long), st);
+    e |= (int)cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStatCount, st);
+    diag_zero_kernel<<<(n + 255) / 256, 256, 0, st>>>(out_matrix, n);
+    if (erp) erp_border_kernel<<<(n + 127) / 128, 128, 0, st>>>(set->data, set->offsets, set->lengths, n, p->erp_gap, cost, L.bs);
+    if (wdtw) wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(L.wt, (double)p->wdtw_g, (double)p->wdtw_wmax);
+    e |= (int)cudaGetLastError();
+    if (e) { sc.release(); return EAP_EDEVICE; }
+    if (items > 0) {
+        eaph::LaunchCtx c;
+        std::memset(&c, 0, sizeof(c));
+        c.job.mode = kModePairwise;
+        c.job.A = dev_set(set, L.bs);
+        c.job.B = dev_set(set, L.bs);
+        c.job.nitems = items;
+        c.job.counter = L.ctr;
+        c.job.cut = L.ub;
+        c.job.out = out_matrix;
+        c.job.stats = L.stats;
+        c.job.wdtw_table = L.wt;
+        c.job.bnd_stride = ((mx + 1) + 31) & ~31;
+        c.kp = make_kparams(p);
+        c.kp.wdtw_w = L.wt;
+        c.kind = p->kind;
+        c.cost = cost;
+        c.prune = prune ? 1 : 0;
+        c.W = choose_w(mx, c.prune);
+        c.sms = sms;
+        c.max_rows = mx;
+        c.stream = st;
+        c.ub = L.ub;
+        if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
+        if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+    }
+    unsigned long long h[kStatCount];
+    if (opt_stats && cudaMemcpyAsync(h, L.stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        sc.release();
+        return EAP_EDEVICE;
+    }
+    sc.release();
+    if (opt_stats) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return EAP_EDEVICE;
+        opt_stats->pairs = h[kStatPairs];
+        opt_stats->pairs_abandoned = h[kStatAbandoned];
+        opt_stats->cells_computed = h[kStatCells];
+        unsigned long long eff = 0, tot = 0, sq = 0;
+        for (int i = 0; i < n; ++i) { tot += (unsigned long long)set->h_lengths[i]; sq += (unsigned long long)set->h_lengths[i] * set->h_lengths[i]; }
+        eff = (tot * tot - sq) / 2;
+        opt_stats->cells_effective = eff;
+    }
+    return EAP_OK;
+}
+
+int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+              const int32_t* ib, const float* cutoff, float* out, int32_t n, void* cuda_stream, eap_stats* opt_stats) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int ma = 0, mb = 0;
+    if ((rc = validate_set(a, &ma)) || (rc = validate_set(b, &mb))) return rc;
+    if (n < 0) return EAP_EINVAL;
+    if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
+    if (n == 0) return EAP_OK;
+    if (!ia || !ib || !out || (p->prune && !cutoff) || a->count == 0 || b->count == 0) return EAP_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
+    const int cost = resolve_cost(p);
+    Scratch sc;
+    auto layout = [&]() {
+        struct { unsigned long long *ctr, *stats; float *ba, *bb, *wt; } L;
+        L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
+        L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
+        L.ba = erp ? (float*)sc.take(sizeof(float) * (size_t)a->data_len) : nullptr;
+        L.bb = erp ? (float*)sc.take(sizeof(float) * (size_t)b->data_len) : nullptr;
+        L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        return L;
+    };
+    layout();
+    if ((rc = sc.alloc(st))) return rc;
+    auto L = layout();
+    int e = 0;
+    e |= (int)cudaMemsetAsync(L.ctr, 0, sizeof(unsigned long long), st);
+    e |= (int)cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStatCount, st);
+    if (erp) {
+        erp_border_kernel<<<(a->count + 127) / 128, 128, 0, st>>>(a->data, a->offsets, a->lengths, a->count, p->erp_gap, cost, L.ba);
+        erp_border_kernel<<<(b->count + 127) / 128, 128, 0, st>>>(b->data, b->offsets, b->lengths, b->count, p->erp_gap, cost, L.bb);
+    }
+    if (wdtw) wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(L.wt, (double)p->wdtw_g, (double)p->wdtw_wmax);
+    e |= (int)cudaGetLastError();
+    if (e) { sc.release(); return EAP_EDEVICE; }
+    eaph::LaunchCtx c;
+    std::memset(&c, 0, sizeof(c));
+    c.job.mode = kModePairs;
+    c.job.A = dev_set(a, L.ba);
+    c.job.B = dev_set(b, L.bb);
+    c.job.nitems = (unsigned long long)n;
+    c.job.counter = L.ctr;
+    c.job.cut = p->prune ? cutoff : nullptr;
+    c.job.out = out;
+    c.job.ia = ia;
+    c.job.ib = ib;
+    c.job.stats = L.stats;
+    c.job.wdtw_table = L.wt;
+    c.job.bnd_stride = ((ma + 1) + 31) & ~31;
+    c.kp = make_kparams(p);
+    c.kp.wdtw_w = L.wt;
+    c.kind = p->kind;
+    c.cost = cost;
+    c.prune = p->prune ? 1 : 0;
+    c.W = choose_w(mb, c.prune);
+    c.sms = sms;
+    c.max_rows = ma;
+    c.stream = st;
+    if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+    unsigned long long h[kStatCount];
+    if (opt_stats && cudaMemcpyAsync(h, L.stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        sc.release();
+        return EAP_EDEVICE;
+    }
+    sc.release();
+    if (opt_stats) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return EAP_EDEVICE;
+        opt_stats->pairs = h[kStatPairs];
+        opt_stats->pairs_abandoned = h[kStatAbandoned];
+        opt_stats->cells_computed = h[kStatCells];
+    }
+    return EAP_OK;
+}
+
+int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+                 const int32_t* ib, float* out, int32_t n, void* cuda_stream) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int ma = 0, mb = 0;
+    if ((rc = validate_set(a, &ma)) || (rc = validate_set(b, &mb))) return rc;
+    if (n < 0) return EAP_EINVAL;
+    if (n == 0) return EAP_OK;
+    if (!ia || !ib || !out || a->count == 0 || b->count == 0) return EAP_EINVAL;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    KParams kp = make_kparams(p);
+    kp.windowed = 1;
+    const int blocks = std::min((n + 7) / 8, sms * 8);
+    lb_keogh_pairs_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(dev_set(a, nullptr), dev_set(b, nullptr), ia, ib,
+                                                                         n, kp, resolve_cost(p), out);
+    return cuda_status((int)cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,416 @@
+// eap_device.cuh -- device side of libeap: per-distance cell functors and the
+// warp-per-pair EAPruned wavefront (sm_103a).
+//
+// Method: Herrmann & Webb, arXiv 2102.05221.  The recurrence is Eq. (Common):
+//   M(i,j) = min( M(i-1,j-1) + Canonical, M(i-1,j) + AlternateRow, M(i,j-1) + AlternateColumn )
+// with each distance's borders and step costs (Section 2.3).
+//
+// Pruning on the GPU.  Alg. 5 prunes with left-to-right row scans
+// (next_start / pruning_point).  A warp cannot scan a row serially, so the
+// kernel uses the fact both of Alg. 5's strategies rest on (Section 3.1/3.2):
+// every step cost is >= 0, so a cell is never below its smallest dependency.
+// Hence (a) a cell whose dependencies all exceed the cut-off exceeds it too,
+// and (b) replacing any value above the cut-off by +inf changes no value at or
+// below the cut-off (the dependency a live cell takes its minimum from is
+// itself <= the cell <= cut-off; float rounding is monotone, so this holds
+// bit for bit).  The kernel therefore prunes whole blocks of cells whenever
+// all their inputs are dead, abandons when no live cell can be reached
+// (the row-abandon of Alg. 5), and returns D exactly when D <= cut-off,
+// +inf otherwise -- the EAPruned contract of Section 2.2.
+//
+// Mapping.  One warp owns one (row series A, column series B) pair.  Columns
+// are cut into panels of 32*W; in a panel lane k owns W consecutive columns
+// and the warp sweeps the panel's rows as a skewed wavefront: at step t lane
+// k computes row r0 + t - k, taking its left input from lane k-1 through
+// __shfl_up_sync (lane 0 takes it from the previous panel's last column,
+// kept in shared memory).  A panel starts at the first row where its left
+// boundary (or top border) can be live -- pruning from the left -- and stops
+// as soon as every cell a later row could depend on is dead -- pruning on
+// the right; the pair is abandoned when a panel hands no live cell to the
+// next one.  The dead-frontier test is a __all_sync over the lanes every
+// few steps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define EAP_FINF __int_as_float(0x7f800000)
+#define EAP_FULL 0xffffffffu
+
+namespace eapd {
+
+// Window value that means "no constraint" (kept small enough that 2*w fits in int).
+constexpr int kNoWindow = 1 << 28;
+
+// ---------------------------------------------------------------------------
+// Parameters as the kernels see them (filled by the host from eap_params).
+// ---------------------------------------------------------------------------
+struct KParams {
+    float wdtw_g, wdtw_wmax;
+    float erp_gap;
+    float msm_c;
+    float twe_nu2;       // 2 * nu (the match cost's nu * (|i-j| + |(i-1)-(j-1)|))
+    float twe_nu, twe_lambda;
+    const float* wdtw_w; // WDTW weights: wdtw_w[2*d + kWdtwOff - L] = wmax / (1 + exp(-g (d - L/2)))
+    int window_abs;      // >= 0 absolute window
+    float window_ratio;  // used when window_abs < 0 (< 0: none)
+    int windowed;        // CDTW / ERP
+    int pad_;
+};
+
+constexpr int kWdtwOff = 1 << 14;   // index offset of the universal WDTW table (covers |2d - L| <= 16384)
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+template <int COST>
+__device__ __forceinline__ float pcost(float a, float b) {
+    const float d = __fsub_rn(a, b);
+    return COST == 0 ? __fmul_rn(d, d) : fabsf(d);
+}
+
+// Window of one pair: w = floor(r * max(L_S, L_T)) in double, or the absolute value.
+__device__ __forceinline__ int pair_window(const KParams& kp, int la, int lb) {
+    if (!kp.windowed) return kNoWindow;
+    long long w;
+    if (kp.window_abs >= 0) w = kp.window_abs;
+    else if (kp.window_ratio >= 0.f) w = (long long)floor((double)kp.window_ratio * (double)(la > lb ? la : lb));
+    else w = kNoWindow;
+    return (int)(w < kNoWindow ? w : kNoWindow);
+}
+
+// ---------------------------------------------------------------------------
+// Cell functors.  Each gives per-column constants (from t_j, t_{j-1}), per-row
+// constants (from s_i, s_{i-1}) and the cell update from the three
+// dependencies.  `dij` is i - j, `fdij` the same as a float.  Every operation
+// uses an explicit-rounding intrinsic, so the compiler never re-associates or
+// contracts differently between the DP and the diagonal upper bound, which
+// evaluate the same functor along the same path.
+// ---------------------------------------------------------------------------
+
+// Eq. DTW (also CDTW, whose window is applied by the caller).
+template <int COST>
+struct FDtw {
+    static constexpr bool kBorders = false;
+    struct Col { float t; };
+    struct Row { float s; const float* wt; };
+    __device__ static Col col(float t, float, const KParams&) { return {t}; }
+    __device__ static Row row(float s, float, const KParams&, const float*) { return {s, nullptr}; }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
+                                 const KParams&) {
+        const float m = min3f(dg, tp, lf);
+        const float d = __fsub_rn(r.s, c.t);
+        return COST == 0 ? __fmaf_rn(d, d, m) : __fadd_rn(fabsf(d), m);
+    }
+};
+
+// Eq. WDTW: the point cost is weighted by w(|i-j|).
+template <int COST>
+struct FWdtw {
+    static constexpr bool kBorders = false;
+    struct Col { float t; };
+    struct Row { float s; const float* wt; };
+    __device__ static Col col(float t, float, const KParams&) { return {t}; }
+    __device__ static Row row(float s, float, const KParams&, const float* wt) { return {s, wt}; }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int dij, float,
+                                 const KParams&) {
+        const float m = min3f(dg, tp, lf);
+        const float wgt = __ldg(r.wt + 2 * abs(dij));
+        return __fmaf_rn(wgt, pcost<COST>(r.s, c.t), m);
+    }
+};
+
+// Eq. ERP: gap value g; borders are the prefix sums of cost(x_k, g).
+template <int COST>
+struct FErp {
+    static constexpr bool kBorders = true;
+    struct Col { float t, ct; };
+    struct Row { float s, cs; };
+    __device__ static Col col(float t, float, const KParams& kp) { return {t, pcost<COST>(t, kp.erp_gap)}; }
+    __device__ static Row row(float s, float, const KParams& kp, const float*) {
+        return {s, pcost<COST>(s, kp.erp_gap)};
+    }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
+                                 const KParams&) {
+        const float d = __fsub_rn(r.s, c.t);
+        const float a = COST == 0 ? __fmaf_rn(d, d, dg) : __fadd_rn(dg, fabsf(d));
+        return min3f(a, __fadd_rn(tp, r.cs), __fadd_rn(lf, c.ct));
+    }
+};
+
+// Eq. MSM with Eq. MSMCost.  C(np, x, y) = c + dist(np, [min(x,y), max(x,y)]);
+// with e = x - np and f = y - np that distance is max(0, min(e,f), -max(e,f)),
+// which is 0 when np lies between x and y and min(|np-x|, |np-y|) otherwise
+// (the same float values as the printed form).
+struct FMsm {
+    static constexpr bool kBorders = false;
+    struct Col { float t, g; };     // g = t_{j-1} - t_j
+    struct Row { float s, e; };     // e = s_{i-1} - s_i
+    __device__ static Col col(float t, float tprev, const KParams&) { return {t, __fsub_rn(tprev, t)}; }
+    __device__ static Row row(float s, float sprev, const KParams&, const float*) {
+        return {s, __fsub_rn(sprev, s)};
+    }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
+                                 const KParams& kp) {
+        const float f = __fsub_rn(c.t, r.s);               // t_j - s_i
+        const float a = __fadd_rn(dg, fabsf(f));           // move: |s_i - t_j|
+        // AlternateRow: np = s_i, x = s_{i-1}, y = t_j  ->  e = s_{i-1}-s_i, f = t_j - s_i
+        const float dt = max3f(0.f, fminf(r.e, f), -fmaxf(r.e, f));
+        const float b = __fadd_rn(tp, __fadd_rn(kp.msm_c, dt));
+        // AlternateColumn: np = t_j, x = s_i, y = t_{j-1}  ->  s_i - t_j = -f, t_{j-1} - t_j = g
+        const float dl = max3f(0.f, fminf(-f, c.g), -fmaxf(-f, c.g));
+        const float cc = __fadd_rn(lf, __fadd_rn(kp.msm_c, dl));
+        return min3f(a, b, cc);
+    }
+};
+
+// Eq. TWE with Eq. TWECost, tau_i = i, s_0 = t_0 = 0.
+template <int COST>
+struct FTwe {
+    static constexpr bool kBorders = false;
+    struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
+    struct Row { float s, sprev, ga; };   // ga = cost(s_i, s_{i-1}) + nu + lambda
+    __device__ static Col col(float t, float tprev, const KParams& kp) {
+        return {t, tprev, __fadd_rn(__fadd_rn(pcost<COST>(t, tprev), kp.twe_nu), kp.twe_lambda)};
+    }
+    __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
+        return {s, sprev, __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda)};
+    }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float fdij,
+                                 const KParams& kp) {
+        const float gm0 = __fadd_rn(pcost<COST>(r.s, c.t), pcost<COST>(r.sprev, c.tprev));
+        const float gm = __fmaf_rn(kp.twe_nu2, fabsf(fdij), gm0);
+        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// One pair, one warp.
+// ---------------------------------------------------------------------------
+struct PairIn {
+    const float* A;      // row series (length La)
+    const float* B;      // column series (length Lb)
+    const float* bA;     // ERP: bA[k] = M(k+1, 0) unwindowed prefix sum over A (else unused)
+    const float* bB;     // ERP: bB[k] = M(0, k+1)
+    const float* wt;     // WDTW: weight of |i-j| = d is wt[2d]
+    const unsigned long long* cut_src;  // best-so-far to refresh from (nn1), or null
+    int La, Lb;
+    int w;               // window (kNoWindow when none)
+    float cut;           // cut-off at the start
+};
+
+// Top border M(0, j) of the column series (j >= 0).
+template <class F>
+__device__ __forceinline__ float hborder(const PairIn& in, int j) {
+    if (j == 0) return 0.f;
+    if (F::kBorders && j <= in.w + 1 && j <= in.Lb) return __ldg(in.bB + j - 1);
+    return EAP_FINF;
+}
+
+// Applies one row of a lane's strip: v[u] holds M(row-1, c0+u) on entry and
+// M(row, c0+u) on exit; dg = M(row-1, c0-1), lf = M(row, c0-1).
+template <class F, int W, bool WIN>
+__device__ __forceinline__ void strip_row(float (&v)[W], const typename F::Col (&cc)[W],
+                                          const typename F::Row& rc, float dg, float lf, int dr, int w,
+                                          const KParams& kp) {
+    const float fdr = (float)dr;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        const float top = v[u];
+        float nv = F::cell(dg, top, lf, rc, cc[u], dr - u, __fsub_rn(fdr, (float)u), kp);
+        if (WIN) {
+            if ((unsigned)(dr - u + w) > (unsigned)(2 * w)) nv = EAP_FINF;
+        }
+        dg = top;
+        v[u] = nv;
+        lf = nv;
+    }
+}
+
+// Returns D(A,B) if it is <= in.cut (PRUNE) or always (Base), else +inf.
+// bnd: this warp's shared-memory column of La+1 floats.  cells: per-lane
+// running count of evaluated cells.
+template <class F, int W, bool PRUNE, bool WIN>
+__device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KParams& kp,
+                           unsigned long long& cells, bool& abandoned) {
+    const int lane = threadIdx.x & 31;
+    const int La = in.La, Lb = in.Lb, w = in.w;
+    constexpr int P = 32 * W;
+    const int npan = (Lb + P - 1) / P;
+    float cut = PRUNE ? in.cut : EAP_FINF;
+    abandoned = false;
+
+    // Left boundary of panel 0 is the vertical border M(r, 0): rows [blo, bhi]
+    // of bnd hold readable values, everything else is +inf.
+    int blo = 1, bhi = 0;
+    if (F::kBorders) {
+        const int vmax = min(La, w + 1);
+        int live = 0;
+        for (int r0 = 1; r0 <= vmax; r0 += 32) {
+            const int r = r0 + lane;
+            const float x = r <= vmax ? __ldg(in.bA + r - 1) : EAP_FINF;
+            if (r <= vmax) bnd[r] = x;
+            live += __popc(__ballot_sync(EAP_FULL, r <= vmax && x <= cut));
+        }
+        if (live > 0) { blo = 1; bhi = live; }   // the border is monotone: live rows are a prefix
+    }
+    __syncwarp();
+
+    for (int p = 0; p < npan; ++p) {
+        const int cf = p * P + 1;
+        const int cl = min(cf + P - 1, Lb);
+        const bool last = (p == npan - 1);
+        if (PRUNE && in.cut_src) {
+            // One lane reads the shared best-so-far and broadcasts it, so the
+            // whole warp takes the same pruning decisions.
+            unsigned long long cv = 0;
+            if (lane == 0) cv = *(volatile const unsigned long long*)in.cut_src;
+            cv = __shfl_sync(EAP_FULL, cv, 0);
+            cut = fminf(cut, __uint_as_float((unsigned)(cv >> 32)));
+        }
+        // Rows of this panel that can hold a live cell start at row 1 if the
+        // top border left of / inside it is live, else at the first live row
+        // of the left boundary (pruning from the left).
+        const bool top_live = hborder<F>(in, cf - 1) <= cut;
+        if (!top_live && blo > bhi) { abandoned = true; return EAP_FINF; }
+        int r0 = top_live ? 1 : blo;
+        int r1 = La;
+        if (WIN) { r0 = max(r0, cf - w); r1 = min(La, cl + w); }
+        if (r0 > r1) {
+            if (last) return EAP_FINF;
+            blo = 1; bhi = 0;
+            continue;
+        }
+
+        const int c0 = cf + lane * W;   // first column of this lane's strip
+        typename F::Col cc[W];
+        float v[W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int c = c0 + u;
+            const float t = c <= Lb ? __ldg(in.B + c - 1) : 0.f;
+            const float tprev = (c >= 2 && c - 1 <= Lb) ? __ldg(in.B + c - 2) : 0.f;
+            cc[u] = F::col(t, tprev, kp);
+            v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
+        }
+        float dg;
+        if (r0 == 1) dg = hborder<F>(in, c0 - 1 <= Lb ? c0 - 1 : Lb + 1);
+        else dg = (lane == 0 && r0 - 1 >= blo && r0 - 1 <= bhi) ? bnd[r0 - 1] : EAP_FINF;
+        const int nvalid = max(0, min(W, Lb - c0 + 1));
+        float out = v[W - 1];
+        float sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
+        float s_next = __ldg(in.A + r0 - 1);
+        const int nsteps = r1 - r0 + 32;
+        int t = 0;
+        for (; t < nsteps; ++t) {
+            const int row = r0 + t - lane;
+            float x = __shfl_up_sync(EAP_FULL, out, 1);
+            if (lane == 0) x = (row >= blo && row <= bhi) ? bnd[row] : EAP_FINF;
+            if (row >= r0 && row <= r1) {
+                const float s = s_next;
+                if (row < r1) s_next = __ldg(in.A + row);
+                const typename F::Row rc = F::row(s, sp, kp, in.wt);
+                strip_row<F, W, WIN>(v, cc, rc, dg, x, row - c0, w, kp);
+                sp = s;
+                dg = x;
+                out = v[W - 1];
+                if (!last && lane == 31) bnd[row] = out;
+            }
+            if (PRUNE && (t & 3) == 3) {
+                bool dead = true;
+                if (row <= r1 && nvalid > 0) {
+                    float m = dg;
+#pragma unroll
+                    for (int u = 0; u < W; ++u) m = (u < nvalid) ? fminf(m, v[u]) : m;
+                    dead = m > cut;
+                    if (lane == 0 && row < bhi) dead = false;
+                }
+                if (__all_sync(EAP_FULL, dead)) { ++t; break; }
+            }
+        }
+        // Rows this lane evaluated in the panel.
+        {
+            const int lastrow = min(r1, r0 + t - 1 - lane);
+            if (lastrow >= r0) cells += (unsigned long long)(lastrow - r0 + 1) * (unsigned)nvalid;
+        }
+        __syncwarp();
+        if (last) {
+            const int off = Lb - cf;         // offset of column Lb inside the panel
+            const int lr = off / W, ur = off % W;
+            float res = EAP_FINF;
+#pragma unroll
+            for (int u = 0; u < W; ++u) if (u == ur) res = v[u];
+            res = __shfl_sync(EAP_FULL, res, lr);
+            const int lastrow = min(r1, r0 + t - 1 - lr);
+            if (lastrow != La) res = EAP_FINF;
+            if (PRUNE && !(res <= cut)) res = EAP_FINF;
+            if (res == EAP_FINF) abandoned = true;
+            return res;
+        }
+        // Live rows of the column handed to the next panel.
+        const int wlast = min(r1, r0 + t - 1 - 31);
+        int lo = 0x7fffffff, hi = -1;
+        for (int r = r0 + lane; r <= wlast; r += 32) {
+            if (bnd[r] <= cut) { lo = min(lo, r); hi = max(hi, r); }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(EAP_FULL, lo, o));
+            hi = max(hi, __shfl_xor_sync(EAP_FULL, hi, o));
+        }
+        if (hi < 0) { blo = 1; bhi = 0; } else { blo = lo; bhi = hi; }
+        __syncwarp();
+    }
+    return EAP_FINF;   // not reached: the last panel returns
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal-path upper bound (Section 3 intro: any warping path's cost bounds
+// D from above).  The path is (1,1)..(m,m), m = min(La,Lb), then straight
+// along the longer axis.  It is evaluated with the same functor as the DP,
+// with the off-path dependencies at +inf, so the DP's value is <= this bound
+// exactly (min and float addition are monotone).
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ float diag_path_cost(const PairIn& in, const KParams& kp) {
+    const int La = in.La, Lb = in.Lb;
+    const int m = min(La, Lb);
+    if (in.w < abs(La - Lb)) return EAP_FINF;
+    float acc = 0.f;   // M(0,0)
+    float sp = 0.f, tp = 0.f;
+    for (int k = 1; k <= m; ++k) {
+        const float s = __ldg(in.A + k - 1), t = __ldg(in.B + k - 1);
+        const typename F::Row rc = F::row(s, sp, kp, in.wt);
+        const typename F::Col c = F::col(t, tp, kp);
+        acc = F::cell(acc, EAP_FINF, EAP_FINF, rc, c, 0, 0.f, kp);
+        sp = s; tp = t;
+    }
+    if (La > Lb) {   // down steps along column Lb (AlternateRow)
+        const typename F::Col c = F::col(__ldg(in.B + Lb - 1), Lb >= 2 ? __ldg(in.B + Lb - 2) : 0.f, kp);
+        for (int i = m + 1; i <= La; ++i) {
+            const float s = __ldg(in.A + i - 1);
+            const typename F::Row rc = F::row(s, sp, kp, in.wt);
+            acc = F::cell(EAP_FINF, acc, EAP_FINF, rc, c, i - Lb, (float)(i - Lb), kp);
+            sp = s;
+        }
+    } else if (Lb > La) {   // right steps along row La (AlternateColumn)
+        const typename F::Row rc = F::row(__ldg(in.A + La - 1), La >= 2 ? __ldg(in.A + La - 2) : 0.f, kp, in.wt);
+        for (int j = m + 1; j <= Lb; ++j) {
+            const float t = __ldg(in.B + j - 1);
+            const typename F::Col c = F::col(t, tp, kp);
+            acc = F::cell(EAP_FINF, EAP_FINF, acc, rc, c, La - j, (float)(La - j), kp);
+            tp = t;
+        }
+    }
+    return acc;
+}
+
+}  // namespace eapd

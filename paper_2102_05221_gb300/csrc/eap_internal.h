@@ -1,0 +1,80 @@
+// eap_internal.h -- host-side interface between the C-ABI layer (eap_api.cu)
+// and the per-distance launch units (eap_dp_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "eap_kernels.cuh"
+
+namespace eaph {
+
+struct LaunchCtx {
+    eapd::DPJob job;
+    eapd::KParams kp;
+    int kind;            // eap_kind
+    int cost;            // resolved: 0 squared, 1 absolute
+    int W;               // strip width per lane (4, 8 or 16)
+    int prune;           // 1 EAPruned, 0 Base
+    int sms;             // multiprocessors of the device
+    int max_rows;        // longest row series (sizes the per-warp shared column)
+    cudaStream_t stream;
+    float* ub;           // diagonal-path upper bounds (output of launch_ub)
+};
+
+// Each returns 0 or a CUDA error code (cudaError_t as int).
+int launch_dp_dtw(const LaunchCtx& c, bool ub_only);
+int launch_dp_cdtw(const LaunchCtx& c, bool ub_only);
+int launch_dp_wdtw(const LaunchCtx& c, bool ub_only);
+int launch_dp_erp(const LaunchCtx& c, bool ub_only);
+int launch_dp_msm(const LaunchCtx& c, bool ub_only);
+int launch_dp_twe(const LaunchCtx& c, bool ub_only);
+
+// Shared launch code for one functor (used by the units above).
+template <class F, int W, bool WIN>
+int run_dp(const LaunchCtx& c) {
+    using namespace eapd;
+    void (*kern)(const DPJob, const KParams) =
+        c.prune ? dp_kernel<F, W, true, WIN> : dp_kernel<F, W, false, WIN>;
+    const size_t smem = (size_t)kWarpsPerBlock * c.job.bnd_stride * sizeof(float);
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    unsigned long long grid = (unsigned long long)per_sm * c.sms;
+    const unsigned long long need = (c.job.nitems + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kThreads, smem, c.stream>>>(c.job, c.kp);
+    return (int)cudaGetLastError();
+}
+
+template <class F>
+int run_ub(const LaunchCtx& c) {
+    using namespace eapd;
+    const unsigned long long total = c.job.mode == kModeNN1
+        ? (unsigned long long)c.job.A.n * c.job.B.n : c.job.nitems;
+    if (total == 0) return 0;
+    unsigned long long blocks = (total + 255) / 256;
+    const unsigned long long cap = (unsigned long long)c.sms * 16;
+    if (blocks > cap) blocks = cap;
+    ub_kernel<F><<<(unsigned)blocks, 256, 0, c.stream>>>(c.job, c.kp, c.ub);
+    return (int)cudaGetLastError();
+}
+
+template <class F, bool WIN>
+int run_kind(const LaunchCtx& c, bool ub_only) {
+    if (ub_only) return run_ub<F>(c);
+    switch (c.W) {
+        case 4: return run_dp<F, 4, WIN>(c);
+        case 8: return run_dp<F, 8, WIN>(c);
+        case 16: return run_dp<F, 16, WIN>(c);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace eaph
