@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark: EAPruned 1-NN for the six elastic distances on one GB300.
+
+Workload (one "step"): 1000 test x 1000 train z-normalised random-walk +
+sine-template series of length 512, 10 classes; 1-NN of every test series
+under DTW, CDTW (window 10%), WDTW (g=0.05, wmax=1), ERP (g=0, window 10%),
+MSM (c=0.5) and TWE (nu=0.001, lambda=1), each through the C ABI
+(eap_nn1).  A query = one (test series, distance) 1-NN search, so one step
+answers 6000 queries.
+
+Prints one JSON line (rank 0).  `value` = queries/s with the inputs resident
+in HBM; `e2e` = the same through eap_nn1_host with pinned host buffers
+(host->device copies and the result read-back inside the timed region);
+`roofline` = the dominant DP kernel's algorithmic FP32 op rate against the
+ALU peak; `cpu_baseline` = the FP64 CPU oracle on a bounded sample.
+
+`--impl reference` times the oracle instead (the program the CUDA path is
+checked against), on the same workload, metric and unit.
+
+Multi-GPU (torchrun): each rank answers its own 1000 test series (a
+different seed) against the same train set; there is no collective on the
+data path (weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+KIND_PARAMS = {
+    "dtw": {}, "cdtw": {"window_ratio": 0.1}, "wdtw": {"wdtw_g": 0.05, "wdtw_wmax": 1.0},
+    "erp": {"erp_gap": 0.0, "window_ratio": 0.1}, "msm": {"msm_c": 0.5},
+    "twe": {"twe_nu": 0.001, "twe_lambda": 1.0},
+}
+# Algorithmic FP32 instructions per cell update of each distance's recurrence
+# (the minimum the cell needs: see the functors in csrc/eap_device.cuh).
+OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 13, "twe": 9}
+# Kernels this library launches per eap_nn1 call: init, upper bound, sort,
+# DP, unpack; ERP adds two border kernels, WDTW one weight table.
+LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 7, "msm": 5, "twe": 5}
+N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
+METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
+UNIT = "queries/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def alu_peak_ops(sms: int, mhz: float) -> float:
+    """FP32 lane-instruction peak: SMs x 128 FP32 lanes x clock."""
+    return sms * 128 * mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="eap_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def make_inputs(rank: int):
+    from paper_2102_05221_gb300 import synth
+    ds = synth.workload_nn1_512(N_TRAIN, N_TEST, seed_offset=0)
+    if rank:
+        # Each rank answers its own test series (weak scaling), same train set.
+        ds_r = synth.workload_nn1_512(N_TRAIN, N_TEST, seed_offset=rank)
+        ds.test = ds_r.test
+    return ds
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 CPU oracle on a bounded sample of the workload.
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_2102_05221_gb300 import synth
+    ds = make_inputs(0)
+    tr = synth.pack(ds.train)
+    cores = os.cpu_count() or 1
+    nq = max(1, min(args.ref_queries, N_TEST))
+    rng = np.random.default_rng(0)
+
+    def step(i):
+        rows = rng.choice(N_TEST, size=nq, replace=False)
+        q = synth.pack([ds.test[r] for r in rows])
+        for kind, kw in KIND_PARAMS.items():
+            O.nn1(O.make_params(kind, **kw), q, tr, nthreads=cores)
+        return nq * len(KIND_PARAMS)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(args.steps):
+        done += step(i)
+    dt = time.perf_counter() - t0
+    value = done / dt
+    sample = f"{nq} random test series x 1000 train x 6 distances per step (FP64 oracle, {cores} threads)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "nn1_six_distances_1000x1000_L512",
+                                            "sample_queries_per_step": nq},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(ds, budget_s: float):
+    """The oracle as it stands, timed on this host's cores on a bounded sample."""
+    import oracle as O
+    from paper_2102_05221_gb300 import synth
+    cores = os.cpu_count() or 1
+    tr = synth.pack(ds.train)
+    # Calibrate on 1 query per distance, then size the sample to the budget.
+    t0 = time.perf_counter()
+    q1 = synth.pack([ds.test[0]])
+    for kind, kw in KIND_PARAMS.items():
+        O.nn1(O.make_params(kind, **kw), q1, tr, nthreads=cores)
+    t1 = time.perf_counter() - t0
+    per_q = t1 / len(KIND_PARAMS)   # one query on one thread ~ cores x this when threads split the queries
+    nq = int(max(cores, min(256, budget_s / max(per_q, 1e-6) * cores / len(KIND_PARAMS))))
+    nq = (nq // cores) * cores or cores
+    q = synth.pack([ds.test[i % N_TEST] for i in range(nq)])
+    t0 = time.perf_counter()
+    for kind, kw in KIND_PARAMS.items():
+        O.nn1(O.make_params(kind, **kw), q, tr, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": nq * len(KIND_PARAMS) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nq} test series x 1000 train x 6 distances, FP64 oracle, {cores} threads, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-queries", type=int, default=4)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kinds", default=",".join(KIND_PARAMS),
+                    help="subset of distances (profiling runs only; the benchmark is all six)")
+    ap.add_argument("--n-test", type=int, default=N_TEST, help="test series per rank (profiling runs only)")
+    args = ap.parse_args()
+    kinds = [k for k in args.kinds.split(",") if k]
+    n_test = args.n_test
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2102_05221_gb300 import eap
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    eap.load()
+    ds = make_inputs(rank)
+    R = eap.SeriesSet.from_matrix(ds.train)
+    ds.test = ds.test[:n_test]
+    Q = eap.SeriesSet.from_matrix(ds.test)
+    stream = torch.cuda.current_stream()
+    params = {k: eap.params(k, **KIND_PARAMS[k]) for k in kinds}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out_idx = {k: torch.empty(n_test, dtype=torch.int32, device="cuda") for k in kinds}
+    out_dist = {k: torch.empty(n_test, dtype=torch.float32, device="cuda") for k in kinds}
+
+    def step(collect):
+        flush.fill_(1.0)   # L2 flush between steps (inputs are smaller than L2)
+        for k in kinds:
+            _, _, st = eap.eap_nn1(params[k], Q, R, stream=stream, with_stats=True,
+                                   out_idx=out_idx[k], out_dist=out_dist[k])
+            if collect is not None:
+                c = collect.setdefault(k, {"dp_ms": 0.0, "cells_computed": 0, "cells_effective": 0, "calls": 0})
+                c["dp_ms"] += st["dp_ms"]
+                c["cells_computed"] += st["cells_computed"]
+                c["cells_effective"] += st["cells_effective"]
+                c["calls"] += 1
+
+    for _ in range(max(3, args.warmup)):
+        step(None)
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    per = {}
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(per)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    t_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    queries = n_test * len(kinds) * args.steps * world
+    value = queries / (t_ms / 1e3)
+
+    # End to end through the host-buffer entry point (pinned host memory).
+    e2e = None
+    if not args.no_e2e:
+        from paper_2102_05221_gb300 import synth
+        trp, tep = synth.pack(ds.train), synth.pack(ds.test)
+
+        def pin(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+        class H:
+            pass
+        hq, hr = H(), H()
+        hq.data, hq.offsets, hq.lengths = pin(tep.data), pin(tep.offsets), pin(tep.lengths)
+        hr.data, hr.offsets, hr.lengths = pin(trp.data), pin(trp.offsets), pin(trp.lengths)
+        hidx = torch.empty(n_test, dtype=torch.int32).pin_memory()
+        hdist = torch.empty(n_test, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            for k in kinds:
+                eap.eap_nn1_host(params[k], hq, hr, out_idx=hidx, out_dist=hdist)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = len(kinds) * (tep.data.nbytes + trp.data.nbytes + tep.offsets.nbytes + tep.lengths.nbytes
+                                  + trp.offsets.nbytes + trp.lengths.nbytes)
+        d2h = len(kinds) * n_test * (4 + 4)
+        e2e = {"value": n_test * len(kinds) * args.steps * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # Dominant kernel: the DP of the distance with the largest device time.
+    props = torch.cuda.get_device_properties(local)
+    peaks = _peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    per_dist = {}
+    for k, c in per.items():
+        s = c["dp_ms"] / 1e3
+        per_dist[k] = {
+            "dp_ms_per_call": c["dp_ms"] / c["calls"],
+            "queries_per_s_dp": n_test * c["calls"] / s if s else None,
+            "effective_cells_per_s": c["cells_effective"] / s if s else None,
+            "computed_cells_per_s": c["cells_computed"] / s if s else None,
+            "computed_over_effective": c["cells_computed"] / max(1, c["cells_effective"]),
+            "ops_per_cell": OPS_PER_CELL[k],
+            "alu_frac": (c["cells_computed"] * OPS_PER_CELL[k] / s) / alu_peak_ops(props.multi_processor_count, max_mhz)
+            if s else None,
+        }
+    dom = max(per, key=lambda k: per[k]["dp_ms"])
+    c = per[dom]
+    s = c["dp_ms"] / 1e3
+    peak = alu_peak_ops(props.multi_processor_count, max_mhz) / 1e12
+    achieved = c["cells_computed"] * OPS_PER_CELL[dom] / s / 1e12
+    roofline = {"bound": "alu", "kernel": f"dp_kernel<{dom}>", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
+                "work_basis": f"{OPS_PER_CELL[dom]} FP32 ops per computed cell"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "nn1_six_distances_1000x1000_L512", "n_train": N_TRAIN, "n_test": N_TEST,
+                   "length": LENGTH, "classes": N_CLASSES, "distances": KIND_PARAMS,
+                   "l2": "flushed between steps (512 MiB write); inputs 4 MB < L2"},
+        "roofline": roofline,
+        "per_distance": per_dist,
+        "gpu_launches": sum(LAUNCHES[k] for k in kinds) * args.steps,
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if kinds != list(KIND_PARAMS) or n_test != N_TEST:
+        line["config"]["profiling_subset"] = {"kinds": kinds, "n_test": n_test}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(ds, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,7 @@ typedef struct {
     uint64_t pairs_abandoned;  /* pairs the DP early-abandoned (returned +inf) */
     uint64_t cells_effective;  /* sum over all pairs of L_S * L_T */
     uint64_t cells_computed;   /* cells the DP kernels evaluated (after pruning) */
+    double   dp_ms;            /* device time of the DP kernel launch(es), CUDA events on the call's stream */
 } eap_stats;
 
 /* ---- entry points -------------------------------------------------------- */

@@ -242,6 +242,26 @@ int choose_w(int max_cols, int prune) {
     return 8;
 }
 
+// DP launch bracketed by CUDA events on the call's stream when timing is asked.
+struct DpTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on = false;
+    explicit DpTimer(bool enable) {
+        if (enable && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) on = true;
+    }
+    void start(cudaStream_t s) { if (on) cudaEventRecord(a, s); }
+    void stop(cudaStream_t s) { if (on) cudaEventRecord(b, s); }
+    double ms() {   // after the stream has been synchronised
+        float t = 0.f;
+        if (on && cudaEventElapsedTime(&t, a, b) == cudaSuccess) return (double)t;
+        return 0.0;
+    }
+    ~DpTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 int dispatch(const eaph::LaunchCtx& c, bool ub_only) {
     switch (c.kind) {
         case EAP_DTW: return eaph::launch_dp_dtw(c, ub_only);
@@ -380,7 +400,10 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
         sort_seed_kernel<<<nq, 512, sizeof(unsigned long long) * chunk, st>>>(d_ub, nr, chunk, d_order, d_best);
         if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
     }
+    DpTimer tm(stats != nullptr);
+    tm.start(st);
     if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+    tm.stop(st);
     unpack_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq, out_idx, out_dist, d_stats);
     if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
     unsigned long long h[kStatCount];
@@ -396,6 +419,7 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
             stats->pairs_abandoned = h[kStatAbandoned];
             stats->cells_computed = h[kStatCells];
             stats->cells_effective = sum_cells(qs, rs);
+            stats->dp_ms = tm.ms();
         }
         if (dev_stats_keep) std::memcpy(dev_stats_keep, h, sizeof(h));
         if (h[kStatErrors]) return EAP_EINTERNAL;
@@ -540,6 +564,7 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
     if (wdtw) wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(L.wt, (double)p->wdtw_g, (double)p->wdtw_wmax);
     e |= (int)cudaGetLastError();
     if (e) { sc.release(); return EAP_EDEVICE; }
+    DpTimer tm(opt_stats != nullptr);
     if (items > 0) {
         eaph::LaunchCtx c;
         std::memset(&c, 0, sizeof(c));
@@ -564,7 +589,9 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
+        tm.start(st);
         if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+        tm.stop(st);
     }
     unsigned long long h[kStatCount];
     if (opt_stats && cudaMemcpyAsync(h, L.stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
@@ -581,6 +608,7 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
         for (int i = 0; i < n; ++i) { tot += (unsigned long long)set->h_lengths[i]; sq += (unsigned long long)set->h_lengths[i] * set->h_lengths[i]; }
         eff = (tot * tot - sq) / 2;
         opt_stats->cells_effective = eff;
+        opt_stats->dp_ms = tm.ms();
     }
     return EAP_OK;
 }
@@ -646,7 +674,10 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
     c.sms = sms;
     c.max_rows = ma;
     c.stream = st;
+    DpTimer tm(opt_stats != nullptr);
+    tm.start(st);
     if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
+    tm.stop(st);
     unsigned long long h[kStatCount];
     if (opt_stats && cudaMemcpyAsync(h, L.stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
         sc.release();
@@ -658,6 +689,7 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
         opt_stats->pairs = h[kStatPairs];
         opt_stats->pairs_abandoned = h[kStatAbandoned];
         opt_stats->cells_computed = h[kStatCells];
+        opt_stats->dp_ms = tm.ms();
     }
     return EAP_OK;
 }

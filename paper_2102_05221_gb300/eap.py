@@ -45,10 +45,10 @@ class eap_series_set(ctypes.Structure):
 class eap_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("pairs_lb_pruned", ctypes.c_uint64),
                 ("pairs_abandoned", ctypes.c_uint64), ("cells_effective", ctypes.c_uint64),
-                ("cells_computed", ctypes.c_uint64)]
+                ("cells_computed", ctypes.c_uint64), ("dp_ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: (float(getattr(self, k)) if k == "dp_ms" else int(getattr(self, k))) for k, _ in self._fields_}
 
 
 class eap_serve_config(ctypes.Structure):
