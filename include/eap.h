@@ -152,6 +152,34 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
 int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
                  const int32_t* ia, const int32_t* ib, float* out, int32_t n, void* cuda_stream);
 
+/* eap_pairs without any allocation.  (The paper has no counterpart: this is
+ * a deployment variant of eap_pairs.)
+ *
+ * For callers that cannot allocate device memory during the call -- code with
+ * a fixed memory budget committed at start-up, code inside a framework that
+ * owns every allocation on the device, or a path where cudaMalloc could block
+ * or fail at the wrong time.  Same arguments and results as eap_pairs; the
+ * scratch it needs (work-queue head, counters, ERP border sums, WDTW weight
+ * table) comes from one 4 MiB array in device memory that is part of the
+ * library and that every device loading libeap holds until the process
+ * exits.  Nothing is allocated by the call: no cudaMalloc, cudaMallocAsync
+ * or cudaFree.
+ *   - Limit: the scratch must fit in 4 MiB.  Only ERP uses more than a few
+ *     KB: it needs 4 bytes per element of both sets (a->data_len +
+ *     b->data_len <= about 1,000,000 floats); WDTW needs 128 KB.  Larger
+ *     requests return EAP_EINVAL without launching anything.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents (the call resets what must start at zero).  Calls that overlap
+ *     on the GPU -- on different streams, or from different host threads --
+ *     race on it; serialise them.
+ *   - opt_stats->dp_ms is left at 0 (timing events would be allocations). */
+int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
+                      const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
+                      void* cuda_stream, eap_stats* opt_stats);
+
 /* ---- serving ------------------------------------------------------------- */
 typedef struct eap_server eap_server;
 

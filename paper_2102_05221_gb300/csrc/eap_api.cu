@@ -714,3 +714,126 @@ int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of eap_pairs.
+//
+// Some callers cannot allocate device memory while they call us: code that
+// runs with a fixed, pre-committed memory budget (no cudaMalloc after
+// start-up), code called from inside a framework that owns every allocation
+// on the device, or code on a path where an allocation could block or fail
+// at the wrong moment.  eap_pairs_noalloc gives them the raw EAPruned pairs
+// call with every piece of scratch (the work-queue head, the work counters,
+// ERP's border prefix sums and WDTW's weight table) taken from one fixed
+// array in device memory that is part of this library, so the call itself
+// allocates nothing.
+// ===========================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB, held by every device that loads libeap
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device ordinal
+
+// Once per device, with that device current: the host-side symbol is only a
+// stand-in, so the kernels must be given the address the runtime reports.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return EAP_EDEVICE;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return EAP_EDEVICE;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return EAP_OK;
+}
+
+}  // namespace
+
+extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
+                                 const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
+                                 void* cuda_stream, eap_stats* opt_stats) {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int ma = 0, mb = 0;
+    if ((rc = validate_set(a, &ma)) || (rc = validate_set(b, &mb))) return rc;
+    if (n < 0) return EAP_EINVAL;
+    if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
+    if (n == 0) return EAP_OK;
+    if (!ia || !ib || !out || (p->prune && !cutoff) || a->count == 0 || b->count == 0) return EAP_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
+    const int cost = resolve_cost(p);
+
+    // Carve the fixed array; reject calls whose scratch would not fit.
+    size_t used = 0;
+    auto take = [&](size_t bytes) { const size_t o = (used + 255) & ~(size_t)255; used = o + bytes; return o; };
+    const size_t o_ctr = take(sizeof(unsigned long long));
+    const size_t o_stats = take(sizeof(unsigned long long) * kStatCount);
+    const size_t o_ba = erp ? take(sizeof(float) * (size_t)a->data_len) : 0;
+    const size_t o_bb = erp ? take(sizeof(float) * (size_t)b->data_len) : 0;
+    const size_t o_wt = wdtw ? take(sizeof(float) * (2 * kWdtwOff + 1)) : 0;
+    if (used > kNoAllocScratchBytes) return EAP_EINVAL;
+    void* base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+    char* s = (char*)base;
+    unsigned long long* d_ctr = (unsigned long long*)(s + o_ctr);
+    unsigned long long* d_stats = (unsigned long long*)(s + o_stats);
+    float* d_ba = erp ? (float*)(s + o_ba) : nullptr;
+    float* d_bb = erp ? (float*)(s + o_bb) : nullptr;
+    float* d_wt = wdtw ? (float*)(s + o_wt) : nullptr;
+
+    // The array keeps the previous call's contents: reset what must start at zero.
+    int e = 0;
+    e |= (int)cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
+    e |= (int)cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * kStatCount, st);
+    if (erp) {
+        erp_border_kernel<<<(a->count + 127) / 128, 128, 0, st>>>(a->data, a->offsets, a->lengths, a->count, p->erp_gap, cost, d_ba);
+        erp_border_kernel<<<(b->count + 127) / 128, 128, 0, st>>>(b->data, b->offsets, b->lengths, b->count, p->erp_gap, cost, d_bb);
+    }
+    if (wdtw) wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(d_wt, (double)p->wdtw_g, (double)p->wdtw_wmax);
+    e |= (int)cudaGetLastError();
+    if (e) return EAP_EDEVICE;
+
+    eaph::LaunchCtx c;
+    std::memset(&c, 0, sizeof(c));
+    c.job.mode = kModePairs;
+    c.job.A = dev_set(a, d_ba);
+    c.job.B = dev_set(b, d_bb);
+    c.job.nitems = (unsigned long long)n;
+    c.job.counter = d_ctr;
+    c.job.cut = p->prune ? cutoff : nullptr;
+    c.job.out = out;
+    c.job.ia = ia;
+    c.job.ib = ib;
+    c.job.stats = d_stats;
+    c.job.wdtw_table = d_wt;
+    c.job.bnd_stride = ((ma + 1) + 31) & ~31;
+    c.kp = make_kparams(p);
+    c.kp.wdtw_w = d_wt;
+    c.kind = p->kind;
+    c.cost = cost;
+    c.prune = p->prune ? 1 : 0;
+    c.W = choose_w(mb, c.prune);
+    c.sms = sms;
+    c.max_rows = ma;
+    c.stream = st;
+    if ((e = dispatch(c, false))) return cuda_status(e);
+    if (opt_stats) {
+        unsigned long long h[kStatCount];
+        if (cudaMemcpyAsync(h, d_stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return EAP_EDEVICE;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return EAP_EDEVICE;
+        opt_stats->pairs = h[kStatPairs];
+        opt_stats->pairs_abandoned = h[kStatAbandoned];
+        opt_stats->cells_computed = h[kStatCells];
+    }
+    return EAP_OK;
+}

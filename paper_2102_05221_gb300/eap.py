@@ -276,3 +276,37 @@ def eap_lb_keogh(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, stream=None)
                           ctypes.c_void_p(ib.data_ptr()), ctypes.c_void_p(out.data_ptr()), n, _stream_ptr(stream))
     _check(rc, "eap_lb_keogh")
     return out
+
+
+def eap_pairs_noalloc(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, cutoff=None, stream=None,
+                      with_stats=False, out=None):
+    """eap_pairs for callers that cannot allocate device memory during the
+    call: the library takes its scratch from a fixed 4 MiB device array
+    instead of allocating.  `ia`, `ib`, `cutoff` and `out` must already be
+    device tensors (int32, int32, float32, float32) when the caller itself
+    cannot allocate; host lists are converted here for convenience."""
+    torch = _torch()
+    lib = load()
+    if not hasattr(lib, "_noalloc_ready"):
+        lib.eap_pairs_noalloc.argtypes = [ctypes.POINTER(eap_params), ctypes.POINTER(eap_series_set),
+                                          ctypes.POINTER(eap_series_set), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.POINTER(eap_stats)]
+        lib.eap_pairs_noalloc.restype = ctypes.c_int
+        lib._noalloc_ready = True
+    dev = a.data.device
+    ia = torch.as_tensor(ia, dtype=torch.int32, device=dev).contiguous()
+    ib = torch.as_tensor(ib, dtype=torch.int32, device=dev).contiguous()
+    n = int(ia.numel())
+    if cutoff is None:
+        cutoff = torch.full((n,), float("inf"), dtype=torch.float32, device=dev)
+    cut = torch.as_tensor(cutoff, dtype=torch.float32, device=dev).contiguous()
+    res = out if out is not None else torch.empty(n, dtype=torch.float32, device=dev)
+    sa, sb = a.struct(), b.struct()
+    st = eap_stats()
+    rc = lib.eap_pairs_noalloc(ctypes.byref(p), ctypes.byref(sa), ctypes.byref(sb), ctypes.c_void_p(ia.data_ptr()),
+                               ctypes.c_void_p(ib.data_ptr()), ctypes.c_void_p(cut.data_ptr()),
+                               ctypes.c_void_p(res.data_ptr()), n, _stream_ptr(stream),
+                               ctypes.byref(st) if with_stats else None)
+    _check(rc, "eap_pairs_noalloc")
+    return (res, st.as_dict()) if with_stats else res
