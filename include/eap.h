@@ -205,6 +205,22 @@ int eap_serve_poll(eap_server* s, uint64_t ticket, int32_t* idx, float* dist);
 int eap_serve_drain(eap_server* s, int32_t timeout_ms);
 int eap_serve_destroy(eap_server* s);
 
+/* Counters and latency of a server.  Latency is measured from
+ * eap_serve_submit to the moment the result is on the host (before any
+ * poll), over the queries completed since the last reset. */
+typedef struct {
+    uint64_t submitted;        /* admitted queries */
+    uint64_t rejected;         /* submits answered EAP_EAGAIN */
+    uint64_t completed;
+    uint64_t batches;          /* device batches launched */
+    double   lat_p50_ms, lat_p99_ms, lat_max_ms;
+    int64_t  inflight_bytes;   /* HBM footprint charged to admitted, unfinished queries */
+    int32_t  inflight;         /* admitted, unfinished queries */
+    int32_t  reserved_;
+} eap_serve_stats;
+/* Fills *out; reset != 0 clears the latency samples and counters afterwards. */
+int eap_serve_stats_get(eap_server* s, eap_serve_stats* out, int32_t reset);
+
 const char* eap_strerror(int code);
 int32_t eap_version(void);
 

@@ -165,6 +165,70 @@ __global__ void lb_keogh_pairs_kernel(const SeriesDev A, const SeriesDev B, cons
     }
 }
 
+// Envelope of every series for LB_Keogh (Section 4.2): U[k] / Lo[k] = max /
+// min of x over |m - k| <= w, w the pair window of an equal-length pair.
+__global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict__ U, float* __restrict__ Lo) {
+    const int s = blockIdx.x;
+    const int L = S.len[s];
+    const float* x = S.data + S.off[s];
+    int w = pair_window(kp, L, L);
+    if (w > L) w = L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        float u = -EAP_FINF, lo = EAP_FINF;
+        const int a = max(0, k - w), b = min(L - 1, k + w);
+        for (int m = a; m <= b; ++m) {
+            const float v = __ldg(x + m);
+            u = fmaxf(u, v);
+            lo = fminf(lo, v);
+        }
+        U[S.off[s] + k] = u;
+        Lo[S.off[s] + k] = lo;
+    }
+}
+
+// Lower bound of every (query, candidate) pair, [q][c]: LB_Keogh(Q, C) (the
+// query's envelope bounds C), and with two_way also LB_Keogh(C, Q); the
+// larger one is kept (the lb-keogh2 cascade of Section 4.2 in one pass).
+// Pairs of unequal length get 0.  The bound is shrunk by `shrink` so float
+// rounding can never lift it above the float32 DP value of the pair.
+__global__ void lb_matrix_kernel(const SeriesDev Q, const SeriesDev R, const float* __restrict__ qU,
+                                 const float* __restrict__ qL, const float* __restrict__ rU,
+                                 const float* __restrict__ rL, int cost, int two_way, float* __restrict__ lb) {
+    const int q = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int Lq = Q.len[q];
+    const int64_t oq = Q.off[q];
+    const float* x = Q.data + oq;
+    const float shrink = 1.0f - (float)(4 * Lq + 16) * 5.9604645e-8f;   // 1 - (4L + 16) 2^-24
+    for (int c = warp; c < R.n; c += nw) {
+        float acc1 = 0.f, acc2 = 0.f;
+        if (R.len[c] == Lq) {
+            const int64_t oc = R.off[c];
+            const float* y = R.data + oc;
+            for (int i = lane; i < Lq; i += 32) {
+                const float yi = __ldg(y + i), u = __ldg(qU + oq + i), lo = __ldg(qL + oq + i);
+                float e = 0.f;
+                if (yi > u) e = cost == 0 ? pcost<0>(yi, u) : pcost<1>(yi, u);
+                else if (yi < lo) e = cost == 0 ? pcost<0>(yi, lo) : pcost<1>(yi, lo);
+                acc1 = __fadd_rn(acc1, e);
+                if (two_way) {
+                    const float xi = __ldg(x + i), u2 = __ldg(rU + oc + i), l2 = __ldg(rL + oc + i);
+                    float e2 = 0.f;
+                    if (xi > u2) e2 = cost == 0 ? pcost<0>(xi, u2) : pcost<1>(xi, u2);
+                    else if (xi < l2) e2 = cost == 0 ? pcost<0>(xi, l2) : pcost<1>(xi, l2);
+                    acc2 = __fadd_rn(acc2, e2);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc1 = __fadd_rn(acc1, __shfl_xor_sync(EAP_FULL, acc1, o));
+                acc2 = __fadd_rn(acc2, __shfl_xor_sync(EAP_FULL, acc2, o));
+            }
+        }
+        if (lane == 0) lb[(size_t)q * R.n + c] = __fmul_rn(fmaxf(acc1, acc2), shrink);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host helpers.
 // ---------------------------------------------------------------------------
@@ -333,10 +397,13 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
     const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
     const int cost = resolve_cost(p);
     const unsigned long long items = (unsigned long long)nq * nr;
+    // Alg. 2's lower bound (LB_Keogh) ahead of the DP: DTW / CDTW, pruned runs.
+    const bool use_lb = prune && p->lb != EAP_LB_NONE && (p->kind == EAP_DTW || p->kind == EAP_CDTW);
+    const bool use_lb2 = use_lb && p->lb == EAP_LB_KEOGH2;
 
     Scratch sc;
     auto layout = [&]() {
-        struct { unsigned long long *best, *ctr, *stats; float* ub; int32_t* order; float *bq, *br, *wt; } L;
+        struct { unsigned long long *best, *ctr, *stats; float* ub; int32_t* order; float *bq, *br, *wt, *lb, *qU, *qL, *rU, *rL; } L;
         L.best = (unsigned long long*)sc.take(sizeof(unsigned long long) * nq);
         L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
         L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
@@ -345,6 +412,11 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
         L.bq = erp ? (float*)sc.take(sizeof(float) * (size_t)qs->data_len) : nullptr;
         L.br = erp ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
         L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        L.lb = use_lb ? (float*)sc.take(sizeof(float) * items) : nullptr;
+        L.qU = use_lb ? (float*)sc.take(sizeof(float) * (size_t)qs->data_len) : nullptr;
+        L.qL = use_lb ? (float*)sc.take(sizeof(float) * (size_t)qs->data_len) : nullptr;
+        L.rU = use_lb2 ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
+        L.rL = use_lb2 ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
         return L;
     };
     layout();
@@ -401,6 +473,17 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
         if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
     }
     DpTimer tm(stats != nullptr);
+    if (use_lb) {
+        KParams ke = make_kparams(p);
+        ke.windowed = 1;
+        if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }   // DTW: the whole series
+        envelope_kernel<<<nq, 128, 0, st>>>(dev_set(qs, nullptr), ke, L.qU, L.qL);
+        if (use_lb2) envelope_kernel<<<nr, 128, 0, st>>>(dev_set(rs, nullptr), ke, L.rU, L.rL);
+        lb_matrix_kernel<<<nq, 256, 0, st>>>(dev_set(qs, nullptr), dev_set(rs, nullptr), L.qU, L.qL, L.rU, L.rL, cost,
+                                             use_lb2 ? 1 : 0, L.lb);
+        if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
+        c.job.lb = L.lb;
+    }
     tm.start(st);
     if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
     tm.stop(st);
@@ -837,3 +920,16 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     }
     return EAP_OK;
 }
+
+// Entry used by the serving loop (eap_serve.cu): 1-NN on device-resident sets
+// on a given stream, no statistics.
+namespace eaph {
+int nn1_device(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t* out_idx,
+               float* out_dist, cudaStream_t stream) {
+    return nn1_impl(p, queries, refs, out_idx, out_dist, stream, nullptr, nullptr);
+}
+}  // namespace eaph
+
+namespace eaph {
+int validate_params_ext(const eap_params* p) { return validate_params(p); }
+}  // namespace eaph

@@ -59,6 +59,10 @@ struct KParams {
 };
 
 constexpr int kWdtwOff = 1 << 14;   // index offset of the universal WDTW table (covers |2d - L| <= 16384)
+template <bool B>
+struct BoolC { static constexpr bool value = B; };
+
+constexpr float kPadValue = 1.0e30f; // value of the columns past a series' end inside a panel
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
@@ -146,29 +150,35 @@ struct FErp {
     }
 };
 
-// Eq. MSM with Eq. MSMCost.  C(np, x, y) = c + dist(np, [min(x,y), max(x,y)]);
-// with e = x - np and f = y - np that distance is max(0, min(e,f), -max(e,f)),
-// which is 0 when np lies between x and y and min(|np-x|, |np-y|) otherwise
-// (the same float values as the printed form).
+// Eq. MSM with Eq. MSMCost.  C(np, x, y) = c + dist(np, [min(x,y), max(x,y)]),
+// dist = 0 when np lies between x and y, else min(|np-x|, |np-y|).  With
+// e = x - np and f = y - np, and the sign of e known in advance, that is
+// dist = clamp(sign(e) * f, 0, |e|): np is outside the interval exactly when
+// f has the sign of e, and then the nearer end is whichever of |e|, |f| is
+// smaller.  For the AlternateRow cost x = s_{i-1} is fixed along a row, for
+// the AlternateColumn cost y = t_{j-1} is fixed along a column, so each cost
+// is one fused multiply-add and one clamp, and c + clamp(u, 0, E) =
+// clamp(c + u, c, c + E) gives the same float as the printed form (every
+// step is exact or one rounding of the same sum).
 struct FMsm {
     static constexpr bool kBorders = false;
-    struct Col { float t, g; };     // g = t_{j-1} - t_j
-    struct Row { float s, e; };     // e = s_{i-1} - s_i
-    __device__ static Col col(float t, float tprev, const KParams&) { return {t, __fsub_rn(tprev, t)}; }
-    __device__ static Row row(float s, float sprev, const KParams&, const float*) {
-        return {s, __fsub_rn(sprev, s)};
+    struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
+    struct Row { float s, sge, ec; };   // e = s_{i-1} - s_i: sge = sign(e), ec = c + |e|
+    __device__ static Col col(float t, float tprev, const KParams& kp) {
+        const float g = __fsub_rn(tprev, t);
+        return {t, g >= 0.f ? -1.f : 1.f, __fadd_rn(kp.msm_c, fabsf(g))};
+    }
+    __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
+        const float e = __fsub_rn(sprev, s);
+        return {s, e >= 0.f ? 1.f : -1.f, __fadd_rn(kp.msm_c, fabsf(e))};
     }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams& kp) {
-        const float f = __fsub_rn(c.t, r.s);               // t_j - s_i
-        const float a = __fadd_rn(dg, fabsf(f));           // move: |s_i - t_j|
-        // AlternateRow: np = s_i, x = s_{i-1}, y = t_j  ->  e = s_{i-1}-s_i, f = t_j - s_i
-        const float dt = max3f(0.f, fminf(r.e, f), -fmaxf(r.e, f));
-        const float b = __fadd_rn(tp, __fadd_rn(kp.msm_c, dt));
-        // AlternateColumn: np = t_j, x = s_i, y = t_{j-1}  ->  s_i - t_j = -f, t_{j-1} - t_j = g
-        const float dl = max3f(0.f, fminf(-f, c.g), -fmaxf(-f, c.g));
-        const float cc = __fadd_rn(lf, __fadd_rn(kp.msm_c, dl));
-        return min3f(a, b, cc);
+        const float f = __fsub_rn(c.t, r.s);                                       // t_j - s_i
+        const float a = __fadd_rn(dg, fabsf(f));                                   // move |s_i - t_j|
+        const float tc = fminf(fmaxf(__fmaf_rn(r.sge, f, kp.msm_c), kp.msm_c), r.ec);   // C(s_i, s_{i-1}, t_j)
+        const float lc = fminf(fmaxf(__fmaf_rn(c.nsg, f, kp.msm_c), kp.msm_c), c.gc);   // C(t_j, s_i, t_{j-1})
+        return min3f(a, __fadd_rn(tp, tc), __fadd_rn(lf, lc));
     }
 };
 
@@ -290,52 +300,94 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             continue;
         }
 
+        // Lane 0 reads the boundary column unconditionally: rows of this panel
+        // outside the live range [blo, bhi] are set to +inf first.
+        for (int r = r0 + lane; r <= r1; r += 32)
+            if (r < blo || r > bhi) bnd[r] = EAP_FINF;
+        __syncwarp();
+
         const int c0 = cf + lane * W;   // first column of this lane's strip
         typename F::Col cc[W];
         float v[W];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
             const int c = c0 + u;
-            const float t = c <= Lb ? __ldg(in.B + c - 1) : 0.f;
-            const float tprev = (c >= 2 && c - 1 <= Lb) ? __ldg(in.B + c - 2) : 0.f;
+            // Columns past Lb get a huge value: their cells stay far above any
+            // finite cut-off and never feed a real cell (they lie to the right).
+            const float t = c <= Lb ? __ldg(in.B + c - 1) : kPadValue;
+            const float tprev = c == 1 ? 0.f : (c - 1 <= Lb ? __ldg(in.B + c - 2) : kPadValue);
             cc[u] = F::col(t, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
         float dg;
         if (r0 == 1) dg = hborder<F>(in, c0 - 1 <= Lb ? c0 - 1 : Lb + 1);
-        else dg = (lane == 0 && r0 - 1 >= blo && r0 - 1 <= bhi) ? bnd[r0 - 1] : EAP_FINF;
+        else dg = (lane == 0) ? bnd[r0 - 1] : EAP_FINF;
+        const bool lane_out = c0 > Lb;             // strip entirely past the last column
         const int nvalid = max(0, min(W, Lb - c0 + 1));
-        float out = v[W - 1];
+        const bool st31 = !last && lane == 31;     // this lane hands its last column to the next panel
         float sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
         float s_next = __ldg(in.A + r0 - 1);
         const int nsteps = r1 - r0 + 32;
-        int t = 0;
-        for (; t < nsteps; ++t) {
+
+        // One step of the skewed wavefront; ACTIVE_CHECK for the ramps, where
+        // some lanes have not started or have finished.
+        auto step = [&](int t, auto active_check) {
             const int row = r0 + t - lane;
-            float x = __shfl_up_sync(EAP_FULL, out, 1);
-            if (lane == 0) x = (row >= blo && row <= bhi) ? bnd[row] : EAP_FINF;
-            if (row >= r0 && row <= r1) {
+            constexpr bool kCheck = decltype(active_check)::value;
+            const bool act = kCheck ? (row >= r0 && row <= r1) : true;
+            const float bv = act ? bnd[row] : EAP_FINF;
+            float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1);
+            if (lane == 0) x = bv;
+            if (act) {
                 const float s = s_next;
-                if (row < r1) s_next = __ldg(in.A + row);
+                s_next = __ldg(in.A + min(row, La - 1));
                 const typename F::Row rc = F::row(s, sp, kp, in.wt);
                 strip_row<F, W, WIN>(v, cc, rc, dg, x, row - c0, w, kp);
                 sp = s;
                 dg = x;
-                out = v[W - 1];
-                if (!last && lane == 31) bnd[row] = out;
+                if (st31) bnd[row] = v[W - 1];
             }
-            if (PRUNE && (t & 3) == 3) {
-                bool dead = true;
-                if (row <= r1 && nvalid > 0) {
-                    float m = dg;
+        };
+        // Dead-frontier vote: every cell a later row of this panel could
+        // depend on (each lane's current strip and left input, and lane 0's
+        // future boundary rows) is above the cut-off.
+        auto frontier_dead = [&](int t) -> bool {
+            const int row = r0 + t - lane;
+            bool dead = true;
+            if (row <= r1 && !lane_out) {
+                float m = dg;
 #pragma unroll
-                    for (int u = 0; u < W; ++u) m = (u < nvalid) ? fminf(m, v[u]) : m;
-                    dead = m > cut;
-                    if (lane == 0 && row < bhi) dead = false;
-                }
-                if (__all_sync(EAP_FULL, dead)) { ++t; break; }
+                for (int u = 0; u < W; ++u) m = fminf(m, v[u]);
+                dead = m > cut;
+                if (lane == 0 && row < bhi) dead = false;
+            }
+            return __all_sync(EAP_FULL, dead);
+        };
+        int done = nsteps;   // steps executed
+        int t = 0;
+        bool stop = false;
+        const int ramp_end = min(31, nsteps);
+        for (; t < ramp_end; ++t) {
+            step(t, BoolC<true>{});
+            if (PRUNE && (t & 3) == 3 && frontier_dead(t)) { done = t + 1; stop = true; break; }
+        }
+        const int steady_end = r1 - r0 + 1;   // steps [31, steady_end) have every lane active
+        if (!stop) {
+            for (; t + 4 <= steady_end; t += 4) {
+                step(t, BoolC<false>{});
+                step(t + 1, BoolC<false>{});
+                step(t + 2, BoolC<false>{});
+                step(t + 3, BoolC<false>{});
+                if (PRUNE && frontier_dead(t + 3)) { done = t + 4; stop = true; break; }
             }
         }
+        if (!stop) {
+            for (; t < nsteps; ++t) {
+                step(t, BoolC<true>{});
+                if (PRUNE && (t & 3) == 3 && frontier_dead(t)) { done = t + 1; break; }
+            }
+        }
+        t = done;
         // Rows this lane evaluated in the panel.
         {
             const int lastrow = min(r1, r0 + t - 1 - lane);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/eap.h"
 #include "eap_kernels.cuh"
 
 namespace eaph {
@@ -20,6 +21,17 @@ struct LaunchCtx {
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
 };
+
+}  // namespace eaph
+
+namespace eaph {
+
+// 1-NN on device-resident sets (eap_api.cu); returns an EAP_* code.
+int nn1_device(const ::eap_params* p, const ::eap_series_set* queries, const ::eap_series_set* refs,
+               int32_t* out_idx, float* out_dist, cudaStream_t stream);
+
+// Parameter validation shared with the serving loop; returns an EAP_* code.
+int validate_params_ext(const ::eap_params* p);
 
 // Each returns 0 or a CUDA error code (cudaError_t as int).
 int launch_dp_dtw(const LaunchCtx& c, bool ub_only);

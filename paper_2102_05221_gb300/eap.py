@@ -310,3 +310,91 @@ def eap_pairs_noalloc(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, cutoff=
                                ctypes.byref(st) if with_stats else None)
     _check(rc, "eap_pairs_noalloc")
     return (res, st.as_dict()) if with_stats else res
+
+
+class eap_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("lat_p50_ms", ctypes.c_double), ("lat_p99_ms", ctypes.c_double),
+                ("lat_max_ms", ctypes.c_double), ("inflight_bytes", ctypes.c_int64), ("inflight", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_"}
+
+
+class Server:
+    """eap_serve_*: resident reference sets, footprint admission, continuous
+    batching of single 1-NN queries submitted from host memory."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=0, max_query_len=0, device=0):
+        _torch()
+        lib = load()
+        if not hasattr(lib, "_serve_ready"):
+            P = ctypes.POINTER
+            lib.eap_serve_stats_get.argtypes = [ctypes.c_void_p, P(eap_serve_stats), ctypes.c_int32]
+            for n in ("eap_serve_add_refset", "eap_serve_submit", "eap_serve_poll", "eap_serve_drain",
+                      "eap_serve_destroy", "eap_serve_stats_get"):
+                getattr(lib, n).restype = ctypes.c_int
+            lib._serve_ready = True
+        self._lib = lib
+        cfg = eap_serve_config(int(hbm_budget_bytes), int(max_inflight), int(max_query_len), int(device), 0)
+        status = ctypes.c_int(0)
+        self._h = lib.eap_serve_create(ctypes.byref(cfg), ctypes.byref(status))
+        if not self._h:
+            raise EapError(status.value, "eap_serve_create")
+        self._keep = []
+
+    def add_refset(self, packed) -> int:
+        data = np.ascontiguousarray(packed.data, dtype=np.float32)
+        off = np.ascontiguousarray(packed.offsets, dtype=np.int64)
+        ln = np.ascontiguousarray(packed.lengths, dtype=np.int32)
+        sid = ctypes.c_int32(-1)
+        rc = self._lib.eap_serve_add_refset(self._h, ctypes.c_void_p(data.ctypes.data), ctypes.c_void_p(off.ctypes.data),
+                                            ctypes.c_void_p(ln.ctypes.data), len(ln), ctypes.byref(sid))
+        _check(rc, "eap_serve_add_refset")
+        return sid.value
+
+    def submit(self, set_id: int, p: eap_params, query) -> int | None:
+        """Ticket, or None when the query is not admitted now (EAP_EAGAIN)."""
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        t = ctypes.c_uint64(0)
+        rc = self._lib.eap_serve_submit(self._h, int(set_id), ctypes.byref(p), ctypes.c_void_p(q.ctypes.data),
+                                        len(q), ctypes.byref(t))
+        if rc == EAP_EAGAIN:
+            return None
+        _check(rc, "eap_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(idx, dist) once done, None before."""
+        idx, dist = ctypes.c_int32(0), ctypes.c_float(0)
+        rc = self._lib.eap_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(idx), ctypes.byref(dist))
+        if rc == EAP_EAGAIN:
+            return None
+        _check(rc, "eap_serve_poll")
+        return idx.value, dist.value
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(self._lib.eap_serve_drain(self._h, int(timeout_ms)), "eap_serve_drain")
+
+    def stats(self, reset: bool = False) -> dict:
+        st = eap_serve_stats()
+        _check(self._lib.eap_serve_stats_get(self._h, ctypes.byref(st), int(reset)), "eap_serve_stats_get")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            self._lib.eap_serve_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -194,3 +194,21 @@ def test_nn1_full_workload_sampled(eap, kind):
     sub = synth.pack([ds.test[r] for r in rows])
     D = O.cross(oracle_params(kind, **kw), sub, tr)
     check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D, rows=rows)
+
+
+@pytest.mark.parametrize("kind", ["dtw", "cdtw"])
+@pytest.mark.parametrize("lb", [1, 2])
+def test_nn1_with_lb_keogh_cascade(eap, kind, lb):
+    """Alg. 2: LB_Keogh (and the two-way lb-keogh2 cascade) ahead of EAPruned
+    changes no result, and skips pairs."""
+    ds = synth.make_dataset(400, 60, 256, 5, 4242)
+    tr, te = synth.pack(ds.train), synth.pack(ds.test)
+    R, Q = _sets(eap, tr, te)
+    kw = {"window_ratio": 0.1} if kind == "cdtw" else {}
+    i0, d0, s0 = eap.eap_nn1(gpu_params(eap, kind, **kw), Q, R, with_stats=True)
+    i1, d1, s1 = eap.eap_nn1(gpu_params(eap, kind, lb=lb, **kw), Q, R, with_stats=True)
+    assert np.array_equal(i0.cpu().numpy(), i1.cpu().numpy())
+    assert np.array_equal(d0.cpu().numpy(), d1.cpu().numpy())
+    assert s1["pairs_lb_pruned"] > 0 and s0["pairs_lb_pruned"] == 0
+    D = O.cross(oracle_params(kind, **kw), te, tr)
+    check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
