@@ -180,6 +180,40 @@ int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_se
                       const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
                       void* cuda_stream, eap_stats* opt_stats);
 
+/* ---- batched uneven workloads ---------------------------------------------
+ * Many independent 1-NN problems (datasets of different lengths, sizes and
+ * distances) in one persistent DP launch: every (task, query, candidate)
+ * item goes through one work queue, tasks ordered longest series first, each
+ * task's candidates ranked by diagonal-path cost and sharing its queries'
+ * cut-offs (the same search as eap_nn1, Alg. 1 with Alg. 5).  All work is
+ * enqueued on the stream with stream-ordered scratch and no host
+ * synchronisation, so the whole call can be captured in a CUDA graph.
+ * Requirements: every task has prune = 1; LB_Keogh options apply to
+ * DTW/CDTW tasks as in eap_nn1. */
+typedef struct {
+    eap_params     params;
+    eap_series_set queries;   /* device + host mirrors */
+    eap_series_set refs;
+    int32_t*       out_idx;   /* device int32[queries.count] */
+    float*         out_dist;  /* device float[queries.count] */
+} eap_nn1_task;
+
+int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cuda_stream, eap_stats* opt_stats);
+
+/* Autotuner for the strip width W (32*W columns per panel) of the warp
+ * wavefront: for each distance and each power-of-two length bucket that
+ * `tasks` contain, times W = 4, 8 and 16 on a sample of that task's own work
+ * (at most 64 queries x 512 candidates) and keeps the fastest in a process-
+ * wide table that eap_nn1, eap_pairwise, eap_pairs and eap_nn1_batch then
+ * use.  Synchronises the stream; call it before any capture.  With a non-NULL
+ * `cache_path` the table is also appended to that text file (one line per
+ * entry: kind cost length_bucket W). */
+int eap_autotune(const eap_nn1_task* tasks, int32_t ntasks, void* cuda_stream, const char* cache_path);
+/* Loads a table written by eap_autotune (missing file: EAP_EINVAL). */
+int eap_autotune_load(const char* cache_path);
+/* Forgets the tuned table (heuristic defaults again). */
+void eap_autotune_reset(void);
+
 /* ---- serving ------------------------------------------------------------- */
 typedef struct eap_server eap_server;
 

@@ -294,16 +294,32 @@ KParams make_kparams(const eap_params* p) {
     return kp;
 }
 
-// Strip width per lane: 32*W columns per panel.  EAP_W overrides (tuning).
-int choose_w(int max_cols, int prune) {
+// Strip width per lane (32*W columns per panel): the autotuned choice for the
+// distance and the power-of-two length bucket when eap_autotune has measured
+// one, else a default; EAP_W overrides both (tuning runs).
+std::mutex g_tune_mu;
+int g_tune[6][2][16] = {};   // [kind][cost][bucket] -> W, 0 = not tuned
+
+int length_bucket(int len) {
+    int b = 0;
+    while ((1 << b) < len && b < 15) ++b;
+    return b;
+}
+
+int choose_w(int kind, int cost, int max_cols, int prune) {
     const char* e = std::getenv("EAP_W");
     if (e) {
         const int w = std::atoi(e);
         if (w == 4 || w == 8 || w == 16) return w;
     }
-    if (max_cols <= 128) return 4;
-    if (!prune && max_cols > 256) return 16;
-    return 8;
+    if (prune && kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        const int t = g_tune[kind][cost][length_bucket(max_cols)];
+        if (t) return t;
+    }
+    if (!prune) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
+    if (kind == EAP_TWE && max_cols > 128) return 8;
+    return 4;
 }
 
 // DP launch bracketed by CUDA events on the call's stream when timing is asked.
@@ -460,7 +476,7 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.kind = p->kind;
     c.cost = cost;
     c.prune = prune ? 1 : 0;
-    c.W = choose_w(mr, c.prune);
+    c.W = choose_w(p->kind, cost, mr, c.prune);
     c.sms = sms;
     c.max_rows = mq;
     c.stream = st;
@@ -666,7 +682,7 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
         c.kind = p->kind;
         c.cost = cost;
         c.prune = prune ? 1 : 0;
-        c.W = choose_w(mx, c.prune);
+        c.W = choose_w(p->kind, cost, mx, c.prune);
         c.sms = sms;
         c.max_rows = mx;
         c.stream = st;
@@ -753,7 +769,7 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune ? 1 : 0;
-    c.W = choose_w(mb, c.prune);
+    c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
     c.stream = st;
@@ -905,7 +921,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune ? 1 : 0;
-    c.W = choose_w(mb, c.prune);
+    c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
     c.stream = st;
@@ -932,4 +948,52 @@ int nn1_device(const eap_params* p, const eap_series_set* queries, const eap_ser
 
 namespace eaph {
 int validate_params_ext(const eap_params* p) { return validate_params(p); }
+}  // namespace eaph
+
+namespace eaph {
+int tune_get(int kind, int cost, int bucket) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune[kind][cost][bucket];
+}
+void tune_set(int kind, int cost, int bucket, int w) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[kind][cost][bucket] = w;
+}
+void tune_reset() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::memset(g_tune, 0, sizeof(g_tune));
+}
+int pick_w(int kind, int cost, int max_cols, int prune) { return choose_w(kind, cost, max_cols, prune); }
+int bucket_of(int len) { return length_bucket(len); }
+int resolve_cost_ext(const eap_params* p) { return resolve_cost(p); }
+int validate_set_ext(const eap_series_set* s, int* max_len) { return validate_set(s, max_len); }
+}  // namespace eaph
+
+// Launch helpers for the batched path (eap_batch.cu), wrapping the kernels above.
+namespace eaph {
+void launch_erp_border(const eap_series_set* s, float gap, int cost, float* border, cudaStream_t st) {
+    if (s->count > 0)
+        erp_border_kernel<<<(s->count + 127) / 128, 128, 0, st>>>(s->data, s->offsets, s->lengths, s->count, gap, cost, border);
+}
+void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st) {
+    wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(tab, (double)g, (double)wmax);
+}
+void launch_lb(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int two_way, float* qU,
+               float* qL, float* rU, float* rL, float* lb, cudaStream_t st) {
+    KParams ke = make_kparams(p);
+    ke.windowed = 1;
+    if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }
+    envelope_kernel<<<qs->count, 128, 0, st>>>(dev_set(qs, nullptr), ke, qU, qL);
+    if (two_way) envelope_kernel<<<rs->count, 128, 0, st>>>(dev_set(rs, nullptr), ke, rU, rL);
+    lb_matrix_kernel<<<qs->count, 256, 0, st>>>(dev_set(qs, nullptr), dev_set(rs, nullptr), qU, qL, rU, rL,
+                                                resolve_cost(p), two_way, lb);
+}
+KParams kparams_of(const eap_params* p) { return make_kparams(p); }
+int nn1_timed(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* idx, float* dist,
+              cudaStream_t st, double* dp_ms) {
+    eap_stats s;
+    const int rc = nn1_impl(p, qs, rs, idx, dist, st, &s, nullptr);
+    if (dp_ms) *dp_ms = s.dp_ms;
+    return rc;
+}
 }  // namespace eaph

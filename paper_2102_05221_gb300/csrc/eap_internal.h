@@ -32,6 +32,24 @@ int nn1_device(const ::eap_params* p, const ::eap_series_set* queries, const ::e
 
 // Parameter validation shared with the serving loop; returns an EAP_* code.
 int validate_params_ext(const ::eap_params* p);
+int validate_set_ext(const ::eap_series_set* s, int* max_len);
+int resolve_cost_ext(const ::eap_params* p);
+
+// Strip-width table filled by the autotuner (eap_api.cu).
+int tune_get(int kind, int cost, int bucket);
+void tune_set(int kind, int cost, int bucket, int w);
+void tune_reset();
+int pick_w(int kind, int cost, int max_cols, int prune);
+int bucket_of(int len);
+
+// Pre-pass launches shared with the batched path (eap_api.cu).
+void launch_erp_border(const ::eap_series_set* s, float gap, int cost, float* border, cudaStream_t st);
+void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st);
+void launch_lb(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int two_way,
+               float* qU, float* qL, float* rU, float* rL, float* lb, cudaStream_t st);
+eapd::KParams kparams_of(const ::eap_params* p);
+int nn1_timed(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int32_t* idx,
+              float* dist, cudaStream_t st, double* dp_ms);
 
 // Each returns 0 or a CUDA error code (cudaError_t as int).
 int launch_dp_dtw(const LaunchCtx& c, bool ub_only);

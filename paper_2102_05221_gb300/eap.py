@@ -398,3 +398,79 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class eap_nn1_task(ctypes.Structure):
+    _fields_ = [("params", eap_params), ("queries", eap_series_set), ("refs", eap_series_set),
+                ("out_idx", ctypes.c_void_p), ("out_dist", ctypes.c_void_p)]
+
+
+def _batch_lib():
+    lib = load()
+    if not hasattr(lib, "_batch_ready"):
+        P = ctypes.POINTER
+        lib.eap_nn1_batch.argtypes = [P(eap_nn1_task), ctypes.c_int32, ctypes.c_void_p, P(eap_stats)]
+        lib.eap_nn1_batch.restype = ctypes.c_int
+        lib.eap_autotune.argtypes = [P(eap_nn1_task), ctypes.c_int32, ctypes.c_void_p, ctypes.c_char_p]
+        lib.eap_autotune.restype = ctypes.c_int
+        lib.eap_autotune_load.argtypes = [ctypes.c_char_p]
+        lib.eap_autotune_load.restype = ctypes.c_int
+        lib.eap_autotune_reset.argtypes = []
+        lib.eap_autotune_reset.restype = None
+        lib._batch_ready = True
+    return lib
+
+
+class Nn1Task:
+    """One 1-NN problem of a batch: parameters, query and reference sets,
+    and device output tensors (allocated here unless given)."""
+
+    def __init__(self, p: eap_params, queries: SeriesSet, refs: SeriesSet, out_idx=None, out_dist=None):
+        torch = _torch()
+        dev = queries.data.device
+        self.p, self.queries, self.refs = p, queries, refs
+        self.out_idx = out_idx if out_idx is not None else torch.empty(queries.count, dtype=torch.int32, device=dev)
+        self.out_dist = out_dist if out_dist is not None else torch.empty(queries.count, dtype=torch.float32,
+                                                                          device=dev)
+
+    def struct(self) -> eap_nn1_task:
+        t = eap_nn1_task()
+        t.params = self.p
+        t.queries = self.queries.struct()
+        t.refs = self.refs.struct()
+        t.out_idx = self.out_idx.data_ptr() if self.queries.count else None
+        t.out_dist = self.out_dist.data_ptr() if self.queries.count else None
+        return t
+
+
+def _task_array(tasks):
+    arr = (eap_nn1_task * max(1, len(tasks)))()
+    for i, t in enumerate(tasks):
+        arr[i] = t.struct()
+    return arr
+
+
+def eap_nn1_batch(tasks, stream=None, with_stats=False):
+    """All tasks' 1-NN searches in one persistent DP launch (results land in
+    each task's out_idx / out_dist)."""
+    lib = _batch_lib()
+    arr = _task_array(tasks)
+    st = eap_stats()
+    rc = lib.eap_nn1_batch(arr, len(tasks), _stream_ptr(stream), ctypes.byref(st) if with_stats else None)
+    _check(rc, "eap_nn1_batch")
+    return st.as_dict() if with_stats else None
+
+
+def eap_autotune(tasks, stream=None, cache_path=None):
+    lib = _batch_lib()
+    arr = _task_array(tasks)
+    rc = lib.eap_autotune(arr, len(tasks), _stream_ptr(stream), cache_path.encode() if cache_path else None)
+    _check(rc, "eap_autotune")
+
+
+def eap_autotune_load(cache_path):
+    _check(_batch_lib().eap_autotune_load(cache_path.encode()), "eap_autotune_load")
+
+
+def eap_autotune_reset():
+    _batch_lib().eap_autotune_reset()
