@@ -44,7 +44,7 @@ KIND_PARAMS = {
 }
 # Algorithmic FP32 instructions per cell update of each distance's recurrence
 # (the minimum the cell needs: see the functors in csrc/eap_device.cuh).
-OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 13, "twe": 9}
+OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 11, "twe": 9}
 # Kernels this library launches per eap_nn1 call: init, upper bound, sort,
 # DP, unpack; ERP adds two border kernels, WDTW one weight table.
 LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 7, "msm": 5, "twe": 5}
@@ -213,6 +213,9 @@ def main():
     ap.add_argument("--kinds", default=",".join(KIND_PARAMS),
                     help="subset of distances (profiling runs only; the benchmark is all six)")
     ap.add_argument("--n-test", type=int, default=N_TEST, help="test series per rank (profiling runs only)")
+    ap.add_argument("--workload", default="nn1_512",
+                    choices=["nn1_512", "unpruned_512", "allpairs_4096", "uneven_64", "serving"],
+                    help="nn1_512 is the benchmark; the others measure the remaining workloads")
     args = ap.parse_args()
     kinds = [k for k in args.kinds.split(",") if k]
     n_test = args.n_test
@@ -222,6 +225,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "nn1_512":
+        return run_other_workload(args)
 
     import numpy as np
     import torch
@@ -381,6 +386,221 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# The other workloads (one JSON line each; the benchmark itself is nn1_512).
+# ---------------------------------------------------------------------------
+def _sync_time(fn, reps=1):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _alu_peak(props):
+    return alu_peak_ops(props.multi_processor_count, float(_peaks().get("sm_max_mhz", 2070.0)))
+
+
+def workload_unpruned_512(args):
+    """Base (unpruned) DP on the 1000 x 1000 x 512 workload: the ALU roofline."""
+    import torch
+
+    from paper_2102_05221_gb300 import eap
+    ds = make_inputs(0)
+    R, Q = eap.SeriesSet.from_matrix(ds.train), eap.SeriesSet.from_matrix(ds.test)
+    props = torch.cuda.get_device_properties(0)
+    peak = _alu_peak(props)
+    out = {}
+    for k in args.kinds.split(","):
+        p = eap.params(k, prune=0, **KIND_PARAMS[k])
+        for _ in range(max(1, args.warmup)):
+            eap.eap_nn1(p, Q, R)
+        ms, cells = 0.0, 0
+        for _ in range(args.steps):
+            _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
+            ms += st["dp_ms"]
+            cells += st["cells_computed"]
+        rate = cells / (ms / 1e3)
+        out[k] = {"dp_ms": ms / args.steps, "cells_per_s": rate, "ops_per_cell": OPS_PER_CELL[k],
+                  "alu_frac": rate * OPS_PER_CELL[k] / peak,
+                  "cells_roofline_per_s": peak / OPS_PER_CELL[k]}
+    return {"metric": "unpruned (Base) DP cell updates/s vs FP32 ALU roofline, 1000 x 1000 x 512",
+            "value": out["dtw"]["cells_per_s"] if "dtw" in out else None, "unit": "cells/s",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "base_dp_1000x1000_L512"}, "per_distance": out,
+            "roofline_peak_ops": peak}
+
+
+def workload_allpairs_4096(args):
+    """256 random walks of length 4096: full DTW and MSM matrices, prune-only."""
+    import torch
+
+    from paper_2102_05221_gb300 import eap, synth
+    x = synth.workload_allpairs_4096()
+    S = eap.SeriesSet.from_matrix(x)
+    n = x.shape[0]
+    pairs = n * (n - 1) // 2
+    props = torch.cuda.get_device_properties(0)
+    res = {}
+    for k in ("dtw", "msm"):
+        p = eap.params(k, **KIND_PARAMS[k])
+        eap.eap_pairwise(p, S, eap.EAP_PRUNE_ONLY)
+        m, st = eap.eap_pairwise(p, S, eap.EAP_PRUNE_ONLY, with_stats=True)
+        t = _sync_time(lambda: eap.eap_pairwise(p, S, eap.EAP_PRUNE_ONLY), reps=args.steps)
+        mb, stb = eap.eap_pairwise(p, S, eap.EAP_BASE, with_stats=True)
+        same = bool(torch.equal(m, mb))
+        res[k] = {"ms": t, "pairs_per_s": pairs / (t / 1e3), "effective_cells_per_s": st["cells_effective"] / (t / 1e3),
+                  "computed_over_effective": st["cells_computed"] / st["cells_effective"],
+                  "base_dp_ms": stb["dp_ms"], "prune_dp_ms": st["dp_ms"],
+                  "base_alu_frac": st["cells_effective"] / (stb["dp_ms"] / 1e3) * OPS_PER_CELL[k] / _alu_peak(props),
+                  "prune_only_equals_base": same}
+    tot = sum(r["ms"] for r in res.values())
+    return {"metric": "all-pairs matrices (DTW + MSM, prune-only), 256 x 4096", "value": 2 * pairs / (tot / 1e3),
+            "unit": "pairs/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "allpairs_256_L4096", "n": n, "length": int(x.shape[1])}, "per_distance": res}
+
+
+def _uneven_tasks(eap, synth):
+    ds = synth.workload_uneven()
+    tasks, meta = [], []
+    for d in ds:
+        R = eap.SeriesSet.from_matrix(d.data.train)
+        Q = eap.SeriesSet.from_matrix(d.data.test)
+        for kind, kw in (("cdtw", {"window_ratio": d.window_ratio, "lb": 2}),
+                         ("erp", {"erp_gap": 0.0, "window_ratio": 0.1}),
+                         ("twe", {"twe_nu": 0.001, "twe_lambda": 1.0})):
+            tasks.append(eap.Nn1Task(eap.params(kind, **kw), Q, R))
+            meta.append((kind, d.length, Q.count, R.count))
+    return tasks, meta
+
+
+def workload_uneven_64(args):
+    """64 datasets (L 24..2048), CDTW+LB_Keogh2, ERP and TWE: one persistent
+    launch per step replayed from a CUDA graph, against one launch per query."""
+    import numpy as np
+    import torch
+
+    from paper_2102_05221_gb300 import eap, synth
+    tasks, meta = _uneven_tasks(eap, synth)
+    nq = sum(t.queries.count for t in tasks)
+    eap.eap_autotune_reset()
+    t0 = time.perf_counter()
+    eap.eap_autotune(tasks)
+    tune_s = time.perf_counter() - t0
+    st = eap.eap_nn1_batch(tasks, with_stats=True)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            eap.eap_nn1_batch(tasks, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(max(1, args.warmup)):
+        g.replay()
+    t_batch = _sync_time(g.replay, reps=args.steps)
+    q_batch = nq / (t_batch / 1e3)
+    # One launch (one eap_nn1 call) per query, plain EAPruned, on a sample.
+    rng = np.random.default_rng(0)
+    sample = [(ti, int(rng.integers(0, t.queries.count))) for ti, t in enumerate(tasks) for _ in range(2)]
+    singles = []
+    for ti, qi in sample:
+        t = tasks[ti]
+        o = int(t.queries.h_offsets[qi])
+        L = int(t.queries.h_lengths[qi])
+        singles.append((t.p, eap.SeriesSet(t.queries.data[o:o + L], [0], [L]), t.refs))
+    for p, Q1, R in singles[:8]:
+        eap.eap_nn1(p, Q1, R)
+
+    def run_singles():
+        for p, Q1, R in singles:
+            eap.eap_nn1(p, Q1, R)
+    t_single = _sync_time(run_singles, reps=1)
+    q_single = len(singles) / (t_single / 1e3)
+    return {"metric": "batched uneven 1-NN queries/s (64 datasets, CDTW+LB_Keogh2, ERP, TWE), one graph-captured launch",
+            "value": q_batch, "unit": "queries/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "ms_per_step": t_batch, "steps": args.steps,
+            "config": {"workload": "uneven_64_datasets_L24_2048", "tasks": len(tasks), "queries_per_step": nq},
+            "one_launch_per_query": {"value": q_single, "unit": "queries/s", "sample_queries": len(singles)},
+            "speedup_vs_one_launch_per_query": q_batch / q_single,
+            "autotune_s": tune_s, "stats_one_step": st}
+
+
+def workload_serving(args):
+    """Serving loop: 8 resident sets, Poisson arrivals, uniform over distances
+    and sets; p50/p99 latency and sustained queries/s per offered rate."""
+    import numpy as np
+
+    from paper_2102_05221_gb300 import eap, synth
+    sizes = {128: 50000, 256: 30000, 512: 20000, 1024: 10000, 2048: 5000, 4096: 3000, 8192: 2000, "mixed": 20000}
+    if args.n_test != N_TEST:   # smaller sets for quick runs
+        f = args.n_test / N_TEST
+        sizes = {k: max(64, int(v * f)) for k, v in sizes.items()}
+    refsets = synth.serving_refsets(sizes)
+    qpool = {L: synth.random_walks(np.random.default_rng(77 + i), 64, L if L != "mixed" else 512).astype(np.float32)
+             for i, L in enumerate(sizes)}
+    rates = [50, 100, 200, 1000, 5000, 20000, 50000]
+    duration = 1.5
+    kinds = list(KIND_PARAMS)
+    params = {k: eap.params(k, **KIND_PARAMS[k]) for k in kinds}
+    out = {}
+    with eap.Server(max_inflight=48) as srv:
+        sids = {L: srv.add_refset(p) for L, p in refsets.items()}
+        keys = list(sids)
+        rng = np.random.default_rng(5)
+        # warm-up: one query per (set, distance)
+        wt = [srv.submit(sids[L], params[k], qpool[L][0]) for L in keys for k in kinds]
+        srv.drain(600000)
+        for t in wt:
+            srv.poll(t)
+        srv.stats(reset=True)
+        for rate in rates:
+            n = int(rate * duration)
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            choice_L = rng.integers(0, len(keys), size=n)
+            choice_k = rng.integers(0, len(kinds), size=n)
+            choice_q = rng.integers(0, 64, size=n)
+            tickets = []
+            t0 = time.perf_counter()
+            for i in range(n):
+                while time.perf_counter() - t0 < arrivals[i]:
+                    pass
+                L = keys[choice_L[i]]
+                t = srv.submit(sids[L], params[kinds[choice_k[i]]], qpool[L][choice_q[i]])
+                if t is not None:
+                    tickets.append(t)
+            srv.drain(600000)
+            t_end = time.perf_counter() - t0
+            for t in tickets:
+                srv.poll(t)
+            st = srv.stats(reset=True)
+            out[str(rate)] = {"offered_per_s": n / arrivals[-1], "admitted": st["submitted"], "rejected": st["rejected"],
+                              "completed_per_s": st["completed"] / t_end, "p50_ms": st["lat_p50_ms"],
+                              "p99_ms": st["lat_p99_ms"], "batches": st["batches"]}
+    best = max(v["completed_per_s"] for v in out.values())
+    return {"metric": "served 1-NN queries/s with p50/p99 latency (8 resident sets, Poisson arrivals)",
+            "value": best, "unit": "queries/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_8_sets", "sizes": {str(k): v for k, v in sizes.items()},
+                       "duration_s_per_rate": duration}, "per_rate": out}
+
+
+def run_other_workload(args):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    from paper_2102_05221_gb300 import eap
+    eap.load()
+    fn = {"unpruned_512": workload_unpruned_512, "allpairs_4096": workload_allpairs_4096,
+          "uneven_64": workload_uneven_64, "serving": workload_serving}[args.workload]
+    line = fn(args)
+    line.setdefault("n_gpus", 1)
+    print(json.dumps(line), flush=True)
     return 0
 
 

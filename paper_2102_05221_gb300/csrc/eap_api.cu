@@ -682,7 +682,9 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
         c.kind = p->kind;
         c.cost = cost;
         c.prune = prune ? 1 : 0;
-        c.W = choose_w(p->kind, cost, mx, c.prune);
+        // Prune-only keeps the Base strip width: a diagonal-path cut-off
+        // prunes far less than a 1-NN best-so-far, so per-cell speed matters more.
+        c.W = choose_w(p->kind, cost, mx, 0);
         c.sms = sms;
         c.max_rows = mx;
         c.stream = st;
