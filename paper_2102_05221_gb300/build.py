@@ -22,6 +22,8 @@ LIB = os.path.join(BUILD, "libeap.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+# Extra nvcc flags for A/B experiments (e.g. "-DEAP_STEADY_UNROLL=5"); part of the build fingerprint.
+EXTRA = os.environ.get("EAP_EXTRA_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:
@@ -41,7 +43,7 @@ def _fingerprint() -> str:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + EXTRA).encode())
     return h.hexdigest()
 
 
@@ -60,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(args):
         src, obj = args
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + EXTRA + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -479,6 +479,7 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.W = choose_w(p->kind, cost, mr, c.prune);
     c.sms = sms;
     c.max_rows = mq;
+    c.max_cols = mr;
     c.stream = st;
     c.ub = d_ub;
     if (prune) {

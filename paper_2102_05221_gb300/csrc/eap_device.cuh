@@ -62,6 +62,12 @@ constexpr int kWdtwOff = 1 << 14;   // index offset of the universal WDTW table 
 template <bool B>
 struct BoolC { static constexpr bool value = B; };
 
+#ifndef EAP_STEADY_UNROLL
+#define EAP_STEADY_UNROLL 0
+#endif
+// Steps per unrolled steady-state iteration (0: W + 1).
+constexpr int kSteadyUnroll = EAP_STEADY_UNROLL;
+
 constexpr float kPadValue = 1.0e30f; // value of the columns past a series' end inside a panel
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
@@ -103,6 +109,7 @@ __device__ __forceinline__ int pair_window(const KParams& kp, int la, int lb) {
 // Eq. DTW (also CDTW, whose window is applied by the caller).
 template <int COST>
 struct FDtw {
+    static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
@@ -119,6 +126,7 @@ struct FDtw {
 // Eq. WDTW: the point cost is weighted by w(|i-j|).
 template <int COST>
 struct FWdtw {
+    static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
@@ -135,6 +143,7 @@ struct FWdtw {
 // Eq. ERP: gap value g; borders are the prefix sums of cost(x_k, g).
 template <int COST>
 struct FErp {
+    static constexpr bool kCarry = false;
     static constexpr bool kBorders = true;
     struct Col { float t, ct; };
     struct Row { float s, cs; };
@@ -161,6 +170,7 @@ struct FErp {
 // clamp(c + u, c, c + E) gives the same float as the printed form (every
 // step is exact or one rounding of the same sum).
 struct FMsm {
+    static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
     struct Row { float s, sge, ec; };   // e = s_{i-1} - s_i: sge = sign(e), ec = c + |e|
@@ -185,6 +195,9 @@ struct FMsm {
 // Eq. TWE with Eq. TWECost, tau_i = i, s_0 = t_0 = 0.
 template <int COST>
 struct FTwe {
+    // cost(s_{i-1}, t_{j-1}) of the match cost is cost(s_i, t_j) of the cell's
+    // diagonal predecessor: the strip carries it from the previous row.
+    static constexpr bool kCarry = true;
     static constexpr bool kBorders = false;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
     struct Row { float s, sprev, ga; };   // ga = cost(s_i, s_{i-1}) + nu + lambda
@@ -200,6 +213,17 @@ struct FTwe {
         const float gm = __fmaf_rn(kp.twe_nu2, fabsf(fdij), gm0);
         return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
     }
+    // The same cell with cost(s_{i-1}, t_{j-1}) given (carry_in) and
+    // cost(s_i, t_j) returned for the next row (carry_out).
+    __device__ static float cell_c(float dg, float tp, float lf, const Row& r, const Col& c, float fdij,
+                                   const KParams& kp, float carry_in, float& carry_out) {
+        const float c1 = pcost<COST>(r.s, c.t);
+        carry_out = c1;
+        const float gm = __fmaf_rn(kp.twe_nu2, fabsf(fdij), __fadd_rn(c1, carry_in));
+        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
+    }
+    __device__ static float carry_first(const Row& r, const Col& c0) { return pcost<COST>(r.sprev, c0.tprev); }
+    __device__ static float carry_init(float sprev, const Col& c) { return pcost<COST>(sprev, c.t); }
 };
 
 // ---------------------------------------------------------------------------
@@ -228,14 +252,23 @@ __device__ __forceinline__ float hborder(const PairIn& in, int j) {
 // Applies one row of a lane's strip: v[u] holds M(row-1, c0+u) on entry and
 // M(row, c0+u) on exit; dg = M(row-1, c0-1), lf = M(row, c0-1).
 template <class F, int W, bool WIN>
-__device__ __forceinline__ void strip_row(float (&v)[W], const typename F::Col (&cc)[W],
+__device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const typename F::Col (&cc)[W],
                                           const typename F::Row& rc, float dg, float lf, int dr, int w,
                                           const KParams& kp) {
     const float fdr = (float)dr;
+    float carry_prev = 0.f;
+    if constexpr (F::kCarry) carry_prev = F::carry_first(rc, cc[0]);
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         const float top = v[u];
-        float nv = F::cell(dg, top, lf, rc, cc[u], dr - u, __fsub_rn(fdr, (float)u), kp);
+        float nv;
+        if constexpr (F::kCarry) {
+            const float cin = carry_prev;
+            carry_prev = cy[u];
+            nv = F::cell_c(dg, top, lf, rc, cc[u], __fsub_rn(fdr, (float)u), kp, cin, cy[u]);
+        } else {
+            nv = F::cell(dg, top, lf, rc, cc[u], dr - u, __fsub_rn(fdr, (float)u), kp);
+        }
         if (WIN) {
             if ((unsigned)(dr - u + w) > (unsigned)(2 * w)) nv = EAP_FINF;
         }
@@ -319,6 +352,15 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             cc[u] = F::col(t, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
+        float cy[W];   // carried per-cell values of the previous row (TWE)
+        {
+            const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if constexpr (F::kCarry) cy[u] = F::carry_init(s_before, cc[u]);
+                else cy[u] = 0.f;
+            }
+        }
         float dg;
         if (r0 == 1) dg = hborder<F>(in, c0 - 1 <= Lb ? c0 - 1 : Lb + 1);
         else dg = (lane == 0) ? bnd[r0 - 1] : EAP_FINF;
@@ -342,7 +384,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                 const float s = s_next;
                 s_next = __ldg(in.A + min(row, La - 1));
                 const typename F::Row rc = F::row(s, sp, kp, in.wt);
-                strip_row<F, W, WIN>(v, cc, rc, dg, x, row - c0, w, kp);
+                strip_row<F, W, WIN>(v, cy, cc, rc, dg, x, row - c0, w, kp);
                 sp = s;
                 dg = x;
                 if (st31) bnd[row] = v[W - 1];
@@ -373,12 +415,14 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         }
         const int steady_end = r1 - r0 + 1;   // steps [31, steady_end) have every lane active
         if (!stop) {
-            for (; t + 4 <= steady_end; t += 4) {
-                step(t, BoolC<false>{});
-                step(t + 1, BoolC<false>{});
-                step(t + 2, BoolC<false>{});
-                step(t + 3, BoolC<false>{});
-                if (PRUNE && frontier_dead(t + 3)) { done = t + 4; stop = true; break; }
+            // Unrolled so that the strip's registers rotate back to their
+            // starting assignment at the back-edge (one new value per cell
+            // per step: W + 1 steps close the cycle).
+            constexpr int U = kSteadyUnroll > 0 ? kSteadyUnroll : W + 1;
+            for (; t + U <= steady_end; t += U) {
+#pragma unroll
+                for (int k = 0; k < U; ++k) step(t + k, BoolC<false>{});
+                if (PRUNE && frontier_dead(t + U - 1)) { done = t + U; stop = true; break; }
             }
         }
         if (!stop) {
@@ -431,6 +475,42 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
 // with the off-path dependencies at +inf, so the DP's value is <= this bound
 // exactly (min and float addition are monotone).
 // ---------------------------------------------------------------------------
+// The same path cost with the column series read from `Bs` (any address space,
+// used by the tiled bound kernel with the candidates staged in shared memory).
+template <class F>
+__device__ float diag_path_cost_b(const PairIn& in, const float* Bs, const KParams& kp) {
+    const int La = in.La, Lb = in.Lb;
+    const int m = min(La, Lb);
+    if (in.w < abs(La - Lb)) return EAP_FINF;
+    float acc = 0.f;
+    float sp = 0.f, tp = 0.f;
+    for (int k = 1; k <= m; ++k) {
+        const float s = __ldg(in.A + k - 1), t = Bs[k - 1];
+        const typename F::Row rc = F::row(s, sp, kp, in.wt);
+        const typename F::Col c = F::col(t, tp, kp);
+        acc = F::cell(acc, EAP_FINF, EAP_FINF, rc, c, 0, 0.f, kp);
+        sp = s; tp = t;
+    }
+    if (La > Lb) {
+        const typename F::Col c = F::col(Bs[Lb - 1], Lb >= 2 ? Bs[Lb - 2] : 0.f, kp);
+        for (int i = m + 1; i <= La; ++i) {
+            const float s = __ldg(in.A + i - 1);
+            const typename F::Row rc = F::row(s, sp, kp, in.wt);
+            acc = F::cell(EAP_FINF, acc, EAP_FINF, rc, c, i - Lb, (float)(i - Lb), kp);
+            sp = s;
+        }
+    } else if (Lb > La) {
+        const typename F::Row rc = F::row(__ldg(in.A + La - 1), La >= 2 ? __ldg(in.A + La - 2) : 0.f, kp, in.wt);
+        for (int j = m + 1; j <= Lb; ++j) {
+            const float t = Bs[j - 1];
+            const typename F::Col c = F::col(t, tp, kp);
+            acc = F::cell(EAP_FINF, EAP_FINF, acc, rc, c, La - j, (float)(La - j), kp);
+            tp = t;
+        }
+    }
+    return acc;
+}
+
 template <class F>
 __device__ float diag_path_cost(const PairIn& in, const KParams& kp) {
     const int La = in.La, Lb = in.Lb;

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "../../include/eap.h"
 #include "eap_kernels.cuh"
 
@@ -18,6 +20,7 @@ struct LaunchCtx {
     int prune;           // 1 EAPruned, 0 Base
     int sms;             // multiprocessors of the device
     int max_rows;        // longest row series (sizes the per-warp shared column)
+    int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
 };
@@ -86,6 +89,20 @@ int run_dp(const LaunchCtx& c) {
 template <class F>
 int run_ub(const LaunchCtx& c) {
     using namespace eapd;
+    if (c.job.mode == kModeNN1 && c.max_cols > 0 && c.max_cols <= 1024) {
+        // Tiled path: 32 candidates per block in shared memory.
+        const size_t smem = (size_t)kUbTileCands * (c.max_cols + 1) * sizeof(float);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(ub_tile_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return (int)e;
+        }
+        const unsigned gx = (unsigned)((c.job.B.n + kUbTileCands - 1) / kUbTileCands);
+        unsigned gy = (unsigned)((c.job.A.n + kUbTileWarps - 1) / kUbTileWarps);
+        const unsigned cap = (unsigned)std::max(1, 8 * c.sms / (int)std::max(1u, gx));
+        if (gy > cap) gy = cap;
+        ub_tile_kernel<F><<<dim3(gx, gy), 32 * kUbTileWarps, smem, c.stream>>>(c.job, c.kp, c.max_cols, c.ub);
+        return (int)cudaGetLastError();
+    }
     const unsigned long long total = c.job.mode == kModeNN1
         ? (unsigned long long)c.job.A.n * c.job.B.n : c.job.nitems;
     if (total == 0) return 0;

@@ -172,4 +172,44 @@ __global__ void ub_kernel(const DPJob job, const KParams kp, float* __restrict__
     }
 }
 
+// Tiled diagonal bounds for 1-NN: a block stages 32 candidates in shared
+// memory (row stride L+1, so lane c reading element k of its own row hits
+// bank (c + k) mod 32 when L is a multiple of 32), then each warp runs one
+// query against those 32 candidates, lane = candidate, in the same order and
+// with the same functor as the untiled kernel (bit-identical bounds).
+constexpr int kUbTileCands = 32;
+constexpr int kUbTileWarps = 8;
+
+template <class F>
+__global__ void __launch_bounds__(32 * kUbTileWarps) ub_tile_kernel(const DPJob job, const KParams kp, int max_lb,
+                                                                     float* __restrict__ ub) {
+    extern __shared__ float tile[];
+    const int stride = max_lb + 1;
+    const int c0 = blockIdx.x * kUbTileCands;
+    const int ncand = min(kUbTileCands, job.B.n - c0);
+    for (int c = threadIdx.x >> 5; c < ncand; c += kUbTileWarps) {
+        const float* src = job.B.data + job.B.off[c0 + c];
+        const int L = job.B.len[c0 + c];
+        for (int k = threadIdx.x & 31; k < L; k += 32) tile[c * stride + k] = __ldg(src + k);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.y * kUbTileWarps + (threadIdx.x >> 5); q < job.A.n; q += gridDim.y * kUbTileWarps) {
+        if (lane < ncand) {
+            const int c = c0 + lane;
+            PairIn in;
+            in.A = job.A.data + job.A.off[q];
+            in.B = nullptr;
+            in.La = job.A.len[q];
+            in.Lb = job.B.len[c];
+            in.bA = in.bB = nullptr;
+            in.wt = job.wdtw_table ? job.wdtw_table + kWdtwOff - max(in.La, in.Lb) : nullptr;
+            in.cut_src = nullptr;
+            in.w = pair_window(kp, in.La, in.Lb);
+            in.cut = EAP_FINF;
+            ub[(size_t)q * job.B.n + c] = diag_path_cost_b<F>(in, tile + lane * stride, kp);
+        }
+    }
+}
+
 }  // namespace eapd
