@@ -570,7 +570,7 @@ def workload_serving(args):
     kinds = list(KIND_PARAMS)
     params = {k: eap.params(k, **KIND_PARAMS[k]) for k in kinds}
     out = {}
-    with eap.Server(max_inflight=48) as srv:
+    with eap.Server(max_inflight=128) as srv:
         sids = {L: srv.add_refset(p) for L, p in refsets.items()}
         keys = list(sids)
         rng = np.random.default_rng(5)

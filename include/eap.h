@@ -200,14 +200,16 @@ typedef struct {
 
 int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cuda_stream, eap_stats* opt_stats);
 
-/* Autotuner for the strip width W (32*W columns per panel) of the warp
- * wavefront: for each distance and each power-of-two length bucket that
- * `tasks` contain, times W = 4, 8 and 16 on a sample of that task's own work
- * (at most 64 queries x 512 candidates) and keeps the fastest in a process-
- * wide table that eap_nn1, eap_pairwise, eap_pairs and eap_nn1_batch then
- * use.  Synchronises the stream; call it before any capture.  With a non-NULL
- * `cache_path` the table is also appended to that text file (one line per
- * entry: kind cost length_bucket W). */
+/* Autotuner for the DP mapping: for each distance and each power-of-two
+ * length bucket that `tasks` contain, times the warp-per-pair wavefront with
+ * strip width W = 4, 8 and 16 (32*W columns per panel) and, for unwindowed
+ * buckets of 2048 and longer, the CTA-per-pair wavefront with W = 4 and 8, on
+ * a sample of that task's own work (at most 64 queries x 512 candidates), and
+ * keeps the fastest in a process-wide table that eap_nn1, eap_pairwise,
+ * eap_pairs and eap_nn1_batch (W only) then use.  Synchronises the stream;
+ * call it before any capture.  With a non-NULL `cache_path` the table is also
+ * appended to that text file (one line per entry: kind cost length_bucket W
+ * mapping, mapping 1 = warp, 2 = CTA). */
 int eap_autotune(const eap_nn1_task* tasks, int32_t ntasks, void* cuda_stream, const char* cache_path);
 /* Loads a table written by eap_autotune (missing file: EAP_EINVAL). */
 int eap_autotune_load(const char* cache_path);

@@ -306,6 +306,26 @@ int length_bucket(int len) {
     return b;
 }
 
+// Warp-per-pair or CTA-per-pair: CTA for unwindowed series of 2048 and more
+// (EAP_MAP=warp|cta overrides).  Windowed bands keep the warp mapping: their
+// panels' rows shift by a panel width, which starves the CTA pipeline.
+int length_bucket(int len);
+std::mutex g_map_mu;
+int g_map[6][2][16] = {};   // [kind][cost][bucket] -> 0 untuned, 1 warp, 2 CTA (set by the autotuner)
+
+int choose_cta(int kind, int cost, int max_rows, int max_cols) {
+    if (kind == EAP_CDTW || kind == EAP_ERP) return 0;
+    const char* e = std::getenv("EAP_MAP");
+    if (e && std::strcmp(e, "warp") == 0) return 0;
+    if (e && std::strcmp(e, "cta") == 0) return 1;
+    if (kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
+        std::lock_guard<std::mutex> lk(g_map_mu);
+        const int m = g_map[kind][cost][length_bucket(std::max(max_rows, max_cols))];
+        if (m) return m == 2 ? 1 : 0;
+    }
+    return (max_rows >= 6144 && max_cols >= 6144) ? 1 : 0;
+}
+
 int choose_w(int kind, int cost, int max_cols, int prune) {
     const char* e = std::getenv("EAP_W");
     if (e) {
@@ -480,6 +500,7 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.sms = sms;
     c.max_rows = mq;
     c.max_cols = mr;
+    c.cta = choose_cta(p->kind, cost, mq, mr);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -688,6 +709,8 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
         c.W = choose_w(p->kind, cost, mx, 0);
         c.sms = sms;
         c.max_rows = mx;
+        c.max_cols = mx;
+        c.cta = choose_cta(p->kind, cost, mx, mx);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -775,6 +798,8 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
     c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
+    c.max_cols = mb;
+    c.cta = choose_cta(p->kind, cost, ma, mb);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -963,8 +988,16 @@ void tune_set(int kind, int cost, int bucket, int w) {
     g_tune[kind][cost][bucket] = w;
 }
 void tune_reset() {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    std::memset(g_tune, 0, sizeof(g_tune));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        std::memset(g_tune, 0, sizeof(g_tune));
+    }
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    std::memset(g_map, 0, sizeof(g_map));
+}
+void map_set(int kind, int cost, int bucket, int m) {
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    g_map[kind][cost][bucket] = m;
 }
 int pick_w(int kind, int cost, int max_cols, int prune) { return choose_w(kind, cost, max_cols, prune); }
 int bucket_of(int len) { return length_bucket(len); }

@@ -496,18 +496,23 @@ extern "C" int eap_autotune(const eap_nn1_task* tasks, int32_t ntasks, void* cud
         rs.count = std::min(rs.count, 512);
         eap_params p = tk.params;
         p.prune = 1;
-        int best_w = 0;
+        int best_w = 0, best_map = 1;
         double best_ms = 1e300;
-        for (int w : {4, 8, 16}) {
-            eaph::tune_set(k.kind, k.cost, k.bucket, w);
+        // Warp-per-pair with W = 4, 8, 16; CTA-per-pair with W = 4, 8 for long unwindowed buckets.
+        const bool try_cta = k.bucket >= 11 && k.kind != EAP_CDTW && k.kind != EAP_ERP;
+        const int cands[5][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
+        for (int ci = 0; ci < (try_cta ? 5 : 3); ++ci) {
+            eaph::tune_set(k.kind, k.cost, k.bucket, cands[ci][0]);
+            eaph::map_set(k.kind, k.cost, k.bucket, cands[ci][1]);
             double ms = 0.0;
             if ((rc = eaph::nn1_timed(&p, &qs, &rs, d_idx, d_dist, st, &ms))) break;
             if ((rc = eaph::nn1_timed(&p, &qs, &rs, d_idx, d_dist, st, &ms))) break;
-            if (ms < best_ms) { best_ms = ms; best_w = w; }
+            if (ms < best_ms) { best_ms = ms; best_w = cands[ci][0]; best_map = cands[ci][1]; }
         }
         if (rc) break;
         eaph::tune_set(k.kind, k.cost, k.bucket, best_w);
-        if (f) std::fprintf(f, "%d %d %d %d\n", k.kind, k.cost, k.bucket, best_w);
+        eaph::map_set(k.kind, k.cost, k.bucket, best_map);
+        if (f) std::fprintf(f, "%d %d %d %d %d\n", k.kind, k.cost, k.bucket, best_w, best_map);
     }
     if (f) std::fclose(f);
     cudaFree(d_idx);
@@ -519,10 +524,13 @@ extern "C" int eap_autotune_load(const char* cache_path) {
     if (!cache_path) return EAP_EINVAL;
     FILE* f = std::fopen(cache_path, "r");
     if (!f) return EAP_EINVAL;
-    int kind, cost, bucket, w;
-    while (std::fscanf(f, "%d %d %d %d", &kind, &cost, &bucket, &w) == 4) {
-        if (kind >= 0 && kind < 6 && (cost == 0 || cost == 1) && bucket >= 0 && bucket < 16 && (w == 4 || w == 8 || w == 16))
+    int kind, cost, bucket, w, m;
+    while (std::fscanf(f, "%d %d %d %d %d", &kind, &cost, &bucket, &w, &m) == 5) {
+        if (kind >= 0 && kind < 6 && (cost == 0 || cost == 1) && bucket >= 0 && bucket < 16 && (w == 4 || w == 8 || w == 16)
+            && (m == 1 || m == 2)) {
             eaph::tune_set(kind, cost, bucket, w);
+            eaph::map_set(kind, cost, bucket, m);
+        }
     }
     std::fclose(f);
     return EAP_OK;

@@ -417,8 +417,9 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         if (!stop) {
             // Unrolled so that the strip's registers rotate back to their
             // starting assignment at the back-edge (one new value per cell
-            // per step: W + 1 steps close the cycle).
-            constexpr int U = kSteadyUnroll > 0 ? kSteadyUnroll : W + 1;
+            // per step: W + 1 steps close the cycle); W = 16 unrolls 4 steps
+            // to keep the code and the register count in check.
+            constexpr int U = kSteadyUnroll > 0 ? kSteadyUnroll : (W <= 8 ? W + 1 : 4);
             for (; t + U <= steady_end; t += U) {
 #pragma unroll
                 for (int k = 0; k < U; ++k) step(t + k, BoolC<false>{});

@@ -21,6 +21,7 @@ struct LaunchCtx {
     int sms;             // multiprocessors of the device
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
+    int cta;             // 1: CTA-per-pair mapping (long, unwindowed series); 0: warp per pair
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
 };
@@ -42,6 +43,7 @@ int resolve_cost_ext(const ::eap_params* p);
 int tune_get(int kind, int cost, int bucket);
 void tune_set(int kind, int cost, int bucket, int w);
 void tune_reset();
+void map_set(int kind, int cost, int bucket, int m);   // 0 untuned, 1 warp, 2 CTA
 int pick_w(int kind, int cost, int max_cols, int prune);
 int bucket_of(int len);
 
@@ -113,9 +115,31 @@ int run_ub(const LaunchCtx& c) {
     return (int)cudaGetLastError();
 }
 
+// CTA-per-pair launch: 8 warps per pair, one full boundary column in shared memory.
+template <class F, int W>
+int run_cta(const LaunchCtx& c) {
+    using namespace eapd;
+    void (*kern)(const DPJob, const KParams) = c.prune ? cta_dp_kernel<F, W, true> : cta_dp_kernel<F, W, false>;
+    const size_t smem = (size_t)(c.max_rows + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCtaThreads, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    unsigned long long grid = (unsigned long long)per_sm * c.sms;
+    if (grid > c.job.nitems) grid = c.job.nitems;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kCtaThreads, smem, c.stream>>>(c.job, c.kp);
+    return (int)cudaGetLastError();
+}
+
 template <class F, bool WIN>
 int run_kind(const LaunchCtx& c, bool ub_only) {
     if (ub_only) return run_ub<F>(c);
+    if constexpr (!WIN) {
+        if (c.cta) return c.W >= 8 ? run_cta<F, 8>(c) : run_cta<F, 4>(c);
+    }
     switch (c.W) {
         case 4: return run_dp<F, 4, WIN>(c);
         case 8: return run_dp<F, 8, WIN>(c);

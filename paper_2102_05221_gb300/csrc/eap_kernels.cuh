@@ -213,3 +213,5 @@ __global__ void __launch_bounds__(32 * kUbTileWarps) ub_tile_kernel(const DPJob 
 }
 
 }  // namespace eapd
+
+#include "eap_cta.cuh"
