@@ -49,6 +49,11 @@ OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 11, "twe": 9}
 # DP, unpack; ERP adds two border kernels, WDTW one weight table.
 LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 7, "msm": 5, "twe": 5}
 N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
+# DRAM bytes (read + write) of the dominant DP launch on this workload, from
+# one ncu capture (profiles/dp_kernel_msm_nn1_512_traffic.md), valid only for
+# the library build whose source fingerprint is recorded with it.
+TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 8783360,
+           "fingerprint": "210d80eba8c904facb4730f6870afd948ba2d848cf4e9e41103846706d50bb28"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -381,8 +386,15 @@ def main():
     s = c["dp_ms"] / 1e3
     peak = alu_peak_ops(props.multi_processor_count, max_mhz) / 1e12
     achieved = c["cells_computed"] * OPS_PER_CELL[dom] / s / 1e12
+    traffic = None
+    try:
+        from paper_2102_05221_gb300 import build as _b
+        if TRAFFIC["kernel"] == f"dp_kernel<{dom}>" and TRAFFIC["fingerprint"] == _b._fingerprint():
+            traffic = TRAFFIC["bytes"]
+    except Exception:
+        traffic = None
     roofline = {"bound": "alu", "kernel": f"dp_kernel<{dom}>", "achieved": achieved, "peak": peak,
-                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "work_basis": f"{OPS_PER_CELL[dom]} FP32 ops per computed cell"}
     line = {

@@ -43,7 +43,8 @@ def _fingerprint() -> str:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS + EXTRA).encode())
+    # Flags without absolute paths, so the fingerprint is the same on every machine.
+    h.update(" ".join(ARCH + NVCC_FLAGS + EXTRA).replace(ROOT, "<root>").encode())
     return h.hexdigest()
 
 

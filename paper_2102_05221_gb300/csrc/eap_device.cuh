@@ -109,6 +109,7 @@ __device__ __forceinline__ int pair_window(const KParams& kp, int la, int lb) {
 // Eq. DTW (also CDTW, whose window is applied by the caller).
 template <int COST>
 struct FDtw {
+    static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t; };
@@ -126,6 +127,10 @@ struct FDtw {
 // Eq. WDTW: the point cost is weighted by w(|i-j|).
 template <int COST>
 struct FWdtw {
+    // The weight of a cell depends on |i-j| only, so the wavefront keeps the
+    // W weights of a lane's strip in registers and shifts them by one cell per
+    // row (cell_w); the table lookup in cell() serves the diagonal bound.
+    static constexpr bool kWeights = true;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t; };
@@ -138,11 +143,15 @@ struct FWdtw {
         const float wgt = __ldg(r.wt + 2 * abs(dij));
         return __fmaf_rn(wgt, pcost<COST>(r.s, c.t), m);
     }
+    __device__ static float cell_w(float dg, float tp, float lf, const Row& r, const Col& c, float wgt) {
+        return __fmaf_rn(wgt, pcost<COST>(r.s, c.t), min3f(dg, tp, lf));
+    }
 };
 
 // Eq. ERP: gap value g; borders are the prefix sums of cost(x_k, g).
 template <int COST>
 struct FErp {
+    static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = true;
     struct Col { float t, ct; };
@@ -170,6 +179,7 @@ struct FErp {
 // clamp(c + u, c, c + E) gives the same float as the printed form (every
 // step is exact or one rounding of the same sum).
 struct FMsm {
+    static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
     struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
@@ -195,6 +205,7 @@ struct FMsm {
 // Eq. TWE with Eq. TWECost, tau_i = i, s_0 = t_0 = 0.
 template <int COST>
 struct FTwe {
+    static constexpr bool kWeights = false;
     // cost(s_{i-1}, t_{j-1}) of the match cost is cost(s_i, t_j) of the cell's
     // diagonal predecessor: the strip carries it from the previous row.
     static constexpr bool kCarry = true;
@@ -252,9 +263,9 @@ __device__ __forceinline__ float hborder(const PairIn& in, int j) {
 // Applies one row of a lane's strip: v[u] holds M(row-1, c0+u) on entry and
 // M(row, c0+u) on exit; dg = M(row-1, c0-1), lf = M(row, c0-1).
 template <class F, int W, bool WIN>
-__device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const typename F::Col (&cc)[W],
-                                          const typename F::Row& rc, float dg, float lf, int dr, int w,
-                                          const KParams& kp) {
+__device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const float (&wr)[W],
+                                          const typename F::Col (&cc)[W], const typename F::Row& rc, float dg,
+                                          float lf, int dr, int w, const KParams& kp) {
     const float fdr = (float)dr;
     float carry_prev = 0.f;
     if constexpr (F::kCarry) carry_prev = F::carry_first(rc, cc[0]);
@@ -266,6 +277,8 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const t
             const float cin = carry_prev;
             carry_prev = cy[u];
             nv = F::cell_c(dg, top, lf, rc, cc[u], __fsub_rn(fdr, (float)u), kp, cin, cy[u]);
+        } else if constexpr (F::kWeights) {
+            nv = F::cell_w(dg, top, lf, rc, cc[u], wr[u]);
         } else {
             nv = F::cell(dg, top, lf, rc, cc[u], dr - u, __fsub_rn(fdr, (float)u), kp);
         }
@@ -275,6 +288,25 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const t
         dg = top;
         v[u] = nv;
         lf = nv;
+    }
+}
+
+// Weights of a strip for the next row: wr[u] <- wr[u-1], wr[0] <- w(|row - c0|).
+template <class F, int W>
+__device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, int row, int c0) {
+    if constexpr (F::kWeights) {
+#pragma unroll
+        for (int u = W - 1; u > 0; --u) wr[u] = wr[u - 1];
+        wr[0] = __ldg(wt + 2 * abs(row - c0));
+    }
+}
+// Weights before a strip's first row r0: wr[u] = w(|r0 - 1 - (c0 + u)|).
+template <class F, int W>
+__device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, int r0, int c0) {
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        if constexpr (F::kWeights) wr[u] = __ldg(wt + 2 * abs(r0 - 1 - c0 - u));
+        else wr[u] = 0.f;
     }
 }
 
@@ -352,6 +384,8 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             cc[u] = F::col(t, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
+        float wr[W];   // weights of the strip's cells for the current row (WDTW)
+        init_weights<F, W>(wr, in.wt, r0, c0);
         float cy[W];   // carried per-cell values of the previous row (TWE)
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
@@ -384,7 +418,8 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                 const float s = s_next;
                 s_next = __ldg(in.A + min(row, La - 1));
                 const typename F::Row rc = F::row(s, sp, kp, in.wt);
-                strip_row<F, W, WIN>(v, cy, cc, rc, dg, x, row - c0, w, kp);
+                shift_weights<F, W>(wr, in.wt, row, c0);
+                strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                 sp = s;
                 dg = x;
                 if (st31) bnd[row] = v[W - 1];
