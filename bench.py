@@ -151,7 +151,7 @@ def run_reference(args, rank, world):
     ds = make_inputs(0)
     tr = synth.pack(ds.train)
     cores = os.cpu_count() or 1
-    nq = max(1, min(args.ref_queries, N_TEST))
+    nq = max(1, min(args.ref_queries or cores, N_TEST))
     rng = np.random.default_rng(0)
 
     def step(i):
@@ -211,7 +211,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-queries", type=int, default=4)
+    ap.add_argument("--ref-queries", type=int, default=0,
+                    help="test series per step of the reference arm (0: one per host core)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
