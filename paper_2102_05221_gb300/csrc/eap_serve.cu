@@ -5,10 +5,10 @@
 // admitted only while the number of queries in flight and their HBM footprint
 // (query bytes + per-candidate scratch of the 1-NN search) stay inside the
 // configured budget, otherwise the submit answers EAP_EAGAIN.  A worker
-// thread forms batches continuously: every admitted query with the same
-// reference set and the same parameters joins one batch, each batch runs as
-// one eap_nn1 search (the persistent work-queue DP) on one of several
-// streams, and new batches are launched while earlier ones are still on the
+// thread forms batches continuously, least work first: every admitted query
+// with the same reference set and the same parameters joins one batch, each
+// batch runs as one eap_nn1 search (the persistent work-queue DP) on one of
+// several streams, and new batches are launched while earlier ones are still on the
 // GPU, so their work overlaps.  A result is the same float32 distance and
 // index whether its query runs alone or in a batch: the DP's value of a pair
 // does not depend on the cut-off it ran with, and ties go to the lowest index.
@@ -32,7 +32,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kSlots = 4;                    // streams with a batch in flight
+constexpr int kSlots = 8;                    // streams with a batch in flight
 constexpr int kBatchMaxQueries = 512;
 constexpr int64_t kBatchMaxFloats = 1 << 22; // query floats per batch (16 MiB)
 
@@ -124,7 +124,14 @@ bool eap_server::launch(Slot& sl) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (pending.empty()) return false;
-        const Req& head = pending.front();
+        // Least work first: the pending query with the fewest cells against its
+        // set (query length x set elements) leads the next batch, so short
+        // queries are not queued behind long ones; ties keep arrival order.
+        auto work = [&](const Req& r) { return (double)r.q.size() * (double)sets[r.set_id].data_len; };
+        auto lead = pending.begin();
+        for (auto it = pending.begin(); it != pending.end(); ++it)
+            if (work(*it) < work(*lead)) lead = it;
+        const Req& head = *lead;
         const int32_t set_id = head.set_id;
         const eap_params p = head.p;
         int64_t floats = 0;
