@@ -74,11 +74,17 @@ typedef struct {
     float   twe_lambda;    /* TWE penalty lambda >= 0 */
     int32_t lb;            /* eap_lb */
     int32_t prune;         /* 1 = EAPruned (Alg. 5 semantics); 0 = Base (Alg. 3: no pruning, no abandoning) */
+    int32_t derivative;    /* 1 = derivative variant (DDTW, DCDTW, DWDTW, ...; Section 2.3): the distance of
+                            * the first-derivative series d_i = ((x_i - x_{i-1}) + (x_{i+1} - x_{i-1})/2)/2
+                            * (Keogh & Pazzani's estimate; the end points copy their neighbour, series of
+                            * one or two points give zeros), computed on the device in float32 into
+                            * stream-ordered scratch of 4 bytes per element of each set; 0 = plain */
 } eap_params;
 
 /* Fills *p with the defaults of the distance: window ratio 0.1 for CDTW/ERP,
  * g = 0.05 and wmax = 1 for WDTW, gap 0 for ERP, c = 0.5 for MSM,
- * nu = 0.001 and lambda = 1 for TWE, default cost, no LB, prune = 1. */
+ * nu = 0.001 and lambda = 1 for TWE, default cost, no LB, prune = 1,
+ * derivative = 0. */
 void eap_params_default(eap_params* p, int32_t kind);
 
 typedef struct {
@@ -164,10 +170,11 @@ int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_
  * library and that every device loading libeap holds until the process
  * exits.  Nothing is allocated by the call: no cudaMalloc, cudaMallocAsync
  * or cudaFree.
- *   - Limit: the scratch must fit in 4 MiB.  Only ERP uses more than a few
- *     KB: it needs 4 bytes per element of both sets (a->data_len +
- *     b->data_len <= about 1,000,000 floats); WDTW needs 128 KB.  Larger
- *     requests return EAP_EINVAL without launching anything.
+ *   - Limit: the scratch must fit in 4 MiB.  Only ERP and the derivative
+ *     variants use more than a few KB: each needs 4 bytes per element of
+ *     both sets (a->data_len + b->data_len <= about 1,000,000 floats, half
+ *     that for a derivative ERP); WDTW needs 128 KB.  Larger requests return
+ *     EAP_EINVAL without launching anything.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
  *     stream capture.

@@ -33,7 +33,7 @@ DEFAULT_COST = {"dtw": COST_SQ, "cdtw": COST_SQ, "wdtw": COST_SQ,
 
 class OrcParams(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("cost", ctypes.c_int32),
-                ("window", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("derivative", ctypes.c_int32),
                 ("window_ratio", ctypes.c_double),
                 ("wdtw_g", ctypes.c_double), ("wdtw_wmax", ctypes.c_double),
                 ("erp_gap", ctypes.c_double), ("msm_c", ctypes.c_double),
@@ -42,11 +42,12 @@ class OrcParams(ctypes.Structure):
 
 def make_params(kind: str, cost=None, window: int = -1, window_ratio: float = -1.0,
                 wdtw_g: float = 0.05, wdtw_wmax: float = 1.0, erp_gap: float = 0.0,
-                msm_c: float = 0.5, twe_nu: float = 0.001, twe_lambda: float = 1.0) -> OrcParams:
+                msm_c: float = 0.5, twe_nu: float = 0.001, twe_lambda: float = 1.0,
+                derivative: int = 0) -> OrcParams:
     """Oracle parameter block.  ``window_ratio`` is widened from float32 so that
     w = floor(r * max(L_S, L_T)) sees the same r as a float32 caller."""
     k = kind.lower()
-    return OrcParams(KINDS[k], DEFAULT_COST[k] if cost is None else int(cost), int(window), 0,
+    return OrcParams(KINDS[k], DEFAULT_COST[k] if cost is None else int(cost), int(window), int(derivative),
                      float(np.float32(window_ratio)) if window_ratio >= 0 else -1.0,
                      float(np.float32(wdtw_g)), float(np.float32(wdtw_wmax)),
                      float(np.float32(erp_gap)), float(np.float32(msm_c)),

@@ -57,7 +57,7 @@ typedef struct {
     int32_t kind;
     int32_t cost;          /* O_COST_SQ / O_COST_ABS */
     int32_t window;        /* >= 0: absolute window; < 0: use window_ratio */
-    int32_t pad_;
+    int32_t derivative;    /* 1: the distance of the first-derivative series (DDTW, DCDTW, ...) */
     double window_ratio;   /* < 0 with window < 0: unconstrained */
     double wdtw_g, wdtw_wmax;
     double erp_gap;
@@ -97,10 +97,43 @@ static double o_wdtw_weight(double wmax, double g, long d, int L) {
     return wmax / (1.0 + exp(-g * ((double)d - (double)L / 2.0)));
 }
 
+/* First-derivative estimate of a series (the derivative distances of Section
+ * 2.3: "taking the first derivative of the series", after Keogh & Pazzani):
+ * d_i = ((x_i - x_{i-1}) + (x_{i+1} - x_{i-1}) / 2) / 2 for interior points;
+ * the first and last points take the estimate of their neighbour; series of
+ * length 1 or 2 have no interior point and give zeros. */
+static void o_derivative(const double* x, int n, double* d) {
+    for (int i = 1; i + 1 < n; i++) d[i] = ((x[i] - x[i - 1]) + (x[i + 1] - x[i - 1]) / 2.0) / 2.0;
+    if (n <= 2) { for (int i = 0; i < n; i++) d[i] = 0.0; return; }
+    d[0] = d[1];
+    d[n - 1] = d[n - 2];
+}
+
+static double orc_distance_d(const orc_params* p, const double* s0, int ls, const double* t0, int lt);
+
 /* Full cost matrix of Eq. (Common) for D(S,T): S on the rows (index i),
  * T on the columns (index j).  Returns M(L_S, L_T). */
 double orc_distance(const orc_params* p, const float* sf, int ls, const float* tf, int lt) {
     if (ls <= 0 || lt <= 0) return NAN;
+    double* a = (double*)malloc(sizeof(double) * (size_t)ls);
+    double* b = (double*)malloc(sizeof(double) * (size_t)lt);
+    for (int i = 0; i < ls; i++) a[i] = (double)sf[i];
+    for (int j = 0; j < lt; j++) b[j] = (double)tf[j];
+    if (p->derivative) {
+        double* da = (double*)malloc(sizeof(double) * (size_t)ls);
+        double* db = (double*)malloc(sizeof(double) * (size_t)lt);
+        o_derivative(a, ls, da);
+        o_derivative(b, lt, db);
+        free(a); free(b);
+        a = da; b = db;
+    }
+    const double r = orc_distance_d(p, a, ls, b, lt);
+    free(a); free(b);
+    return r;
+}
+
+/* The definition itself, on series already in double. */
+static double orc_distance_d(const orc_params* p, const double* s0, int ls, const double* t0, int lt) {
     const long w = o_window(p, ls, lt);
     const int L = ls > lt ? ls : lt;
     const int k = p->kind;
@@ -110,8 +143,8 @@ double orc_distance(const orc_params* p, const float* sf, int ls, const float* t
     double* t = (double*)calloc((size_t)lt + 1, sizeof(double));
     double* prev = (double*)malloc(((size_t)lt + 1) * sizeof(double));
     double* curr = (double*)malloc(((size_t)lt + 1) * sizeof(double));
-    for (int i = 1; i <= ls; i++) s[i] = (double)sf[i - 1];
-    for (int j = 1; j <= lt; j++) t[j] = (double)tf[j - 1];
+    for (int i = 1; i <= ls; i++) s[i] = s0[i - 1];
+    for (int j = 1; j <= lt; j++) t[j] = t0[j - 1];
 
     /* Row 0: M(0,0) = 0 and the horizontal border (InitHBorder). */
     curr[0] = 0.0;
@@ -245,6 +278,15 @@ double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* t
     double* c = (double*)calloc((size_t)Lco + 1, sizeof(double));
     for (int i = 1; i <= Lli; i++) r[i] = (double)lif[i - 1];
     for (int j = 1; j <= Lco; j++) c[j] = (double)cof[j - 1];
+    if (p->derivative) {
+        double* dr = (double*)malloc(sizeof(double) * (size_t)Lli);
+        double* dc = (double*)malloc(sizeof(double) * (size_t)Lco);
+        o_derivative(r + 1, Lli, dr);
+        o_derivative(c + 1, Lco, dc);
+        for (int i = 1; i <= Lli; i++) r[i] = dr[i - 1];
+        for (int j = 1; j <= Lco; j++) c[j] = dc[j - 1];
+        free(dr); free(dc);
+    }
     o_ctx x = {p, r, c, Lli};
     double* prev = (double*)malloc(((size_t)Lco + 1) * sizeof(double));
     double* curr = (double*)malloc(((size_t)Lco + 1) * sizeof(double));

@@ -109,6 +109,30 @@ __global__ void erp_border_kernel(const float* __restrict__ data, const int64_t*
 
 // Universal WDTW weight table (Eq. WDTW): entry kWdtwOff + u holds
 // wmax / (1 + exp(-g u / 2)), u = 2d - L, evaluated in double and rounded.
+// First-derivative estimate of every series of a set, for the derivative
+// distances (DDTW and the others, Section 2.3; Keogh & Pazzani's estimate):
+// d_i = ((x_i - x_{i-1}) + (x_{i+1} - x_{i-1}) / 2) / 2 at interior points,
+// the first and last points take their neighbour's estimate, and series of
+// one or two points (no interior point) give zeros.  Blocks stride over the
+// series, threads over the points (coalesced); out has the layout of data.
+__global__ void derivative_kernel(const float* __restrict__ data, const int64_t* __restrict__ off,
+                                  const int32_t* __restrict__ len, int n, float* __restrict__ out) {
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        const float* x = data + off[s];
+        float* d = out + off[s];
+        const int L = len[s];
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            float v = 0.f;
+            if (L > 2) {
+                const int k = min(max(i, 1), L - 2);
+                const float xl = __ldg(x + k - 1), xc = __ldg(x + k), xr = __ldg(x + k + 1);
+                v = __fmul_rn(__fadd_rn(__fsub_rn(xc, xl), __fmul_rn(__fsub_rn(xr, xl), 0.5f)), 0.5f);
+            }
+            d[i] = v;
+        }
+    }
+}
+
 __global__ void wdtw_table_kernel(float* tab, double g, double wmax) {
     const int n = 2 * kWdtwOff + 1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -252,6 +276,7 @@ int validate_params(const eap_params* p) {
     if (p->kind < EAP_DTW || p->kind > EAP_TWE) return EAP_EINVAL;
     if (p->cost != EAP_COST_DEFAULT && p->cost != EAP_COST_SQ && p->cost != EAP_COST_ABS) return EAP_EINVAL;
     if (p->prune != 0 && p->prune != 1) return EAP_EINVAL;
+    if (p->derivative != 0 && p->derivative != 1) return EAP_EINVAL;
     if (p->lb < EAP_LB_NONE || p->lb > EAP_LB_KEOGH2) return EAP_EINVAL;
     if (!finite_f(p->window_ratio)) return EAP_EINVAL;
     if (p->kind == EAP_WDTW && !(finite_f(p->wdtw_g) && p->wdtw_g >= 0.f && finite_f(p->wdtw_wmax) && p->wdtw_wmax > 0.f))
@@ -412,8 +437,50 @@ unsigned long long sum_cells(const eap_series_set* a, const eap_series_set* b) {
 
 int cuda_status(int e) { return e == 0 ? EAP_OK : EAP_EDEVICE; }
 
+void launch_derivative_set(const eap_series_set* s, float* out, int sms, cudaStream_t st) {
+    if (s->count <= 0) return;
+    const int blocks = std::min(s->count, std::max(1, sms) * 8);
+    derivative_kernel<<<blocks, 128, 0, st>>>(s->data, s->offsets, s->lengths, s->count, out);
+}
+
+// The derivative variants (p->derivative = 1) run `body` unchanged on copies
+// of the sets whose data are the first-derivative series (derivative_kernel),
+// with p->derivative cleared; the copies live in one stream-ordered block
+// freed after the body.  b may be null (single-set calls) or equal to a.
+template <class Body>
+int with_derivative(const eap_params* p, const eap_series_set* a, const eap_series_set* b, cudaStream_t st,
+                    Body&& body) {
+    if (!p || p->derivative == 0) return body(p, a, b);
+    int rc = validate_params(p);
+    if (rc) return rc;
+    int ma = 0, mb = 0;
+    if ((rc = validate_set(a, &ma)) || (b && b != a && (rc = validate_set(b, &mb)))) return rc;
+    eap_params q = *p;
+    q.derivative = 0;
+    const bool own_b = b && b != a;
+    const size_t na = a->count > 0 ? (size_t)a->data_len : 0;
+    const size_t nb = own_b && b->count > 0 ? (size_t)b->data_len : 0;
+    const size_t ob = (na + 63) & ~(size_t)63;
+    float* buf = nullptr;
+    if (na + nb > 0 && cudaMallocAsync((void**)&buf, sizeof(float) * (ob + nb), st) != cudaSuccess) {
+        cudaGetLastError();
+        return EAP_ENOMEM;
+    }
+    const int sms = device_sms();
+    eap_series_set da = *a, db = own_b ? *b : *a;
+    if (na) { da.data = buf; launch_derivative_set(a, buf, sms, st); }
+    if (nb) { db.data = buf + ob; launch_derivative_set(b, buf + ob, sms, st); }
+    if (cudaGetLastError() != cudaSuccess) {
+        if (buf) cudaFreeAsync(buf, st);
+        return EAP_EDEVICE;
+    }
+    rc = body(&q, &da, b ? (own_b ? &db : &da) : nullptr);
+    if (buf) cudaFreeAsync(buf, st);
+    return rc;
+}
+
 // Shared body of 1-NN for device-resident sets.
-int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
+int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
              float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep) {
     int rc = validate_params(p);
     if (rc) return rc;
@@ -548,6 +615,20 @@ int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set
     return EAP_OK;
 }
 
+int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
+             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep) {
+    return with_derivative(p, qs, rs, st, [&](const eap_params* q, const eap_series_set* a, const eap_series_set* b) {
+        return nn1_core(q, a, b, out_idx, out_dist, st, stats, dev_stats_keep);
+    });
+}
+
+int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode, cudaStream_t st,
+                  eap_stats* opt_stats);
+int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+               const int32_t* ib, const float* cutoff, float* out, int32_t n, cudaStream_t st, eap_stats* opt_stats);
+int lb_keogh_core(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+                  const int32_t* ib, float* out, int32_t n, cudaStream_t st);
+
 }  // namespace
 
 // ===========================================================================
@@ -647,6 +728,36 @@ int eap_nn1_host(const eap_params* p, const float* q_data, const int64_t* q_offs
 
 int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode, void* cuda_stream,
                  eap_stats* opt_stats) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    return with_derivative(p, set, nullptr, st, [&](const eap_params* q, const eap_series_set* a, const eap_series_set*) {
+        return pairwise_core(q, a, out_matrix, mode, st, opt_stats);
+    });
+}
+
+int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+              const int32_t* ib, const float* cutoff, float* out, int32_t n, void* cuda_stream, eap_stats* opt_stats) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (n <= 0) return pairs_core(p, a, b, ia, ib, cutoff, out, n, st, opt_stats);   // validation only, nothing to derive
+    return with_derivative(p, a, b, st, [&](const eap_params* q, const eap_series_set* x, const eap_series_set* y) {
+        return pairs_core(q, x, y, ia, ib, cutoff, out, n, st, opt_stats);
+    });
+}
+
+int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+                 const int32_t* ib, float* out, int32_t n, void* cuda_stream) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (n <= 0) return lb_keogh_core(p, a, b, ia, ib, out, n, st);
+    return with_derivative(p, a, b, st, [&](const eap_params* q, const eap_series_set* x, const eap_series_set* y) {
+        return lb_keogh_core(q, x, y, ia, ib, out, n, st);
+    });
+}
+
+}  // extern "C"
+
+namespace {
+
+int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode, cudaStream_t st,
+                  eap_stats* opt_stats) {
     int rc = validate_params(p);
     if (rc) return rc;
     int mx = 0;
@@ -656,7 +767,6 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     const int n = set->count;
     if (n == 0) return EAP_OK;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const int sms = device_sms();
     if (sms <= 0) return EAP_EDEVICE;
     const bool prune = mode == EAP_PRUNE_ONLY;
@@ -738,8 +848,8 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
     return EAP_OK;
 }
 
-int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
-              const int32_t* ib, const float* cutoff, float* out, int32_t n, void* cuda_stream, eap_stats* opt_stats) {
+int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+               const int32_t* ib, const float* cutoff, float* out, int32_t n, cudaStream_t st, eap_stats* opt_stats) {
     int rc = validate_params(p);
     if (rc) return rc;
     int ma = 0, mb = 0;
@@ -748,7 +858,6 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     if (n == 0) return EAP_OK;
     if (!ia || !ib || !out || (p->prune && !cutoff) || a->count == 0 || b->count == 0) return EAP_EINVAL;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const int sms = device_sms();
     if (sms <= 0) return EAP_EDEVICE;
     const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
@@ -821,8 +930,8 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
     return EAP_OK;
 }
 
-int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
-                 const int32_t* ib, float* out, int32_t n, void* cuda_stream) {
+int lb_keogh_core(const eap_params* p, const eap_series_set* a, const eap_series_set* b, const int32_t* ia,
+                  const int32_t* ib, float* out, int32_t n, cudaStream_t st) {
     int rc = validate_params(p);
     if (rc) return rc;
     int ma = 0, mb = 0;
@@ -835,12 +944,12 @@ int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_
     KParams kp = make_kparams(p);
     kp.windowed = 1;
     const int blocks = std::min((n + 7) / 8, sms * 8);
-    lb_keogh_pairs_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(dev_set(a, nullptr), dev_set(b, nullptr), ia, ib,
-                                                                         n, kp, resolve_cost(p), out);
+    lb_keogh_pairs_kernel<<<blocks, 256, 0, st>>>(dev_set(a, nullptr), dev_set(b, nullptr), ia, ib, n, kp,
+                                                  resolve_cost(p), out);
     return cuda_status((int)cudaGetLastError());
 }
 
-}  // extern "C"
+}  // namespace
 
 // ===========================================================================
 // Allocation-free variant of eap_pairs.
@@ -908,6 +1017,9 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     const size_t o_ba = erp ? take(sizeof(float) * (size_t)a->data_len) : 0;
     const size_t o_bb = erp ? take(sizeof(float) * (size_t)b->data_len) : 0;
     const size_t o_wt = wdtw ? take(sizeof(float) * (2 * kWdtwOff + 1)) : 0;
+    const bool deriv = p->derivative != 0;
+    const size_t o_da = deriv ? take(sizeof(float) * (size_t)a->data_len) : 0;
+    const size_t o_db = deriv ? take(sizeof(float) * (size_t)b->data_len) : 0;
     if (used > kNoAllocScratchBytes) return EAP_EINVAL;
     void* base = nullptr;
     if ((rc = noalloc_scratch(&base))) return rc;
@@ -922,6 +1034,16 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     int e = 0;
     e |= (int)cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
     e |= (int)cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * kStatCount, st);
+    // Derivative variants: the sets' first-derivative series, also from the fixed array.
+    eap_series_set da = *a, db = *b;
+    if (deriv) {
+        da.data = (const float*)(s + o_da);
+        db.data = (const float*)(s + o_db);
+        launch_derivative_set(a, (float*)(s + o_da), sms, st);
+        launch_derivative_set(b, (float*)(s + o_db), sms, st);
+        a = &da;
+        b = &db;
+    }
     if (erp) {
         erp_border_kernel<<<(a->count + 127) / 128, 128, 0, st>>>(a->data, a->offsets, a->lengths, a->count, p->erp_gap, cost, d_ba);
         erp_border_kernel<<<(b->count + 127) / 128, 128, 0, st>>>(b->data, b->offsets, b->lengths, b->count, p->erp_gap, cost, d_bb);
@@ -1010,6 +1132,9 @@ namespace eaph {
 void launch_erp_border(const eap_series_set* s, float gap, int cost, float* border, cudaStream_t st) {
     if (s->count > 0)
         erp_border_kernel<<<(s->count + 127) / 128, 128, 0, st>>>(s->data, s->offsets, s->lengths, s->count, gap, cost, border);
+}
+void launch_derivative(const eap_series_set* s, float* out, cudaStream_t st) {
+    launch_derivative_set(s, out, device_sms(), st);
 }
 void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st) {
     wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(tab, (double)g, (double)wmax);

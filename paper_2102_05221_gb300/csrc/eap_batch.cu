@@ -260,7 +260,7 @@ struct HostTask {
     int src;            // index in the caller's array
     int fn, W, cost;
     int nq, nr, mq, mr;
-    bool erp, wdtw, lb, lb2;
+    bool erp, wdtw, lb, lb2, deriv;
 };
 
 int device_sms_b() {
@@ -300,6 +300,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         h.wdtw = tk.params.kind == EAP_WDTW;
         h.lb = tk.params.lb != EAP_LB_NONE && (tk.params.kind == EAP_DTW || tk.params.kind == EAP_CDTW);
         h.lb2 = h.lb && tk.params.lb == EAP_LB_KEOGH2;
+        h.deriv = tk.params.derivative != 0;
         ht.push_back(h);
         max_rows = std::max(max_rows, mq);
     }
@@ -320,7 +321,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
     const size_t o_tasks = take(sizeof(TaskDev) * nt);
     const size_t o_ctr = take(sizeof(unsigned long long));
     const size_t o_stats = take(sizeof(unsigned long long) * kStatCount);
-    struct Off { size_t best, ub, order, lb, qU, qL, rU, rL, bq, br, wt; };
+    struct Off { size_t best, ub, order, lb, qU, qL, rU, rL, bq, br, wt, dq, dr; };
     std::vector<Off> off(nt);
     for (int k = 0; k < nt; ++k) {
         const HostTask& h = ht[k];
@@ -345,9 +346,27 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
             o.br = take(sizeof(float) * std::max<int64_t>(tk.refs.data_len, 1));
         }
         if (h.wdtw) o.wt = take(sizeof(float) * (2 * kWdtwOff + 1));
+        if (h.deriv) {
+            o.dq = take(sizeof(float) * (size_t)tk.queries.data_len);
+            o.dr = take(sizeof(float) * std::max<int64_t>(tk.refs.data_len, 1));
+        }
+    }
+    // The sets each task's kernels read: the caller's, or (derivative variants,
+    // Section 2.3) copies whose data are the first-derivative series.
+    std::vector<eap_series_set> qset(nt), rset(nt);
+    for (int k = 0; k < nt; ++k) {
+        qset[k] = tasks[ht[k].src].queries;
+        rset[k] = tasks[ht[k].src].refs;
     }
     char* base = nullptr;
     if (cudaMallocAsync((void**)&base, used, st) != cudaSuccess) { cudaGetLastError(); return EAP_ENOMEM; }
+    for (int k = 0; k < nt; ++k) {
+        if (!ht[k].deriv) continue;
+        eaph::launch_derivative(&qset[k], (float*)(base + off[k].dq), st);
+        eaph::launch_derivative(&rset[k], (float*)(base + off[k].dr), st);
+        qset[k].data = (const float*)(base + off[k].dq);
+        rset[k].data = (const float*)(base + off[k].dr);
+    }
 
     std::vector<TaskDev> td(nt);
     unsigned long long items = 0;
@@ -360,8 +379,8 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         std::memset(&t, 0, sizeof(t));
         float* bq = h.erp ? (float*)(base + o.bq) : nullptr;
         float* br = h.erp ? (float*)(base + o.br) : nullptr;
-        t.A = SeriesDev{tk.queries.data, tk.queries.offsets, tk.queries.lengths, bq, tk.queries.count};
-        t.B = SeriesDev{tk.refs.data, tk.refs.offsets, tk.refs.lengths, br, tk.refs.count};
+        t.A = SeriesDev{qset[k].data, tk.queries.offsets, tk.queries.lengths, bq, tk.queries.count};
+        t.B = SeriesDev{rset[k].data, tk.refs.offsets, tk.refs.lengths, br, tk.refs.count};
         t.kp = eaph::kparams_of(&tk.params);
         t.wt = h.wdtw ? (const float*)(base + o.wt) : nullptr;
         t.best = (unsigned long long*)(base + o.best);
@@ -399,12 +418,12 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         const eap_nn1_task& tk = tasks[h.src];
         const Off& o = off[k];
         if (h.erp) {
-            eaph::launch_erp_border(&tk.queries, tk.params.erp_gap, h.cost, (float*)(base + o.bq), st);
-            eaph::launch_erp_border(&tk.refs, tk.params.erp_gap, h.cost, (float*)(base + o.br), st);
+            eaph::launch_erp_border(&qset[k], tk.params.erp_gap, h.cost, (float*)(base + o.bq), st);
+            eaph::launch_erp_border(&rset[k], tk.params.erp_gap, h.cost, (float*)(base + o.br), st);
         }
         if (h.wdtw) eaph::launch_wdtw_table((float*)(base + o.wt), tk.params.wdtw_g, tk.params.wdtw_wmax, st);
         if (h.lb && h.nr > 0)
-            eaph::launch_lb(&tk.params, &tk.queries, &tk.refs, h.lb2 ? 1 : 0, (float*)(base + o.qU), (float*)(base + o.qL),
+            eaph::launch_lb(&tk.params, &qset[k], &rset[k], h.lb2 ? 1 : 0, (float*)(base + o.qU), (float*)(base + o.qL),
                             h.lb2 ? (float*)(base + o.rU) : nullptr, h.lb2 ? (float*)(base + o.rL) : nullptr,
                             (float*)(base + o.lb), st);
     }

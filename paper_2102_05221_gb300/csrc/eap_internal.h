@@ -50,6 +50,8 @@ int bucket_of(int len);
 // Pre-pass launches shared with the batched path (eap_api.cu).
 void launch_erp_border(const ::eap_series_set* s, float gap, int cost, float* border, cudaStream_t st);
 void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st);
+// First-derivative series of every series of s into out (same layout as s->data).
+void launch_derivative(const ::eap_series_set* s, float* out, cudaStream_t st);
 void launch_lb(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int two_way,
                float* qU, float* qL, float* rU, float* rL, float* lb, cudaStream_t st);
 eapd::KParams kparams_of(const ::eap_params* p);

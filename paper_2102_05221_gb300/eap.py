@@ -33,7 +33,8 @@ class eap_params(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("cost", ctypes.c_int32), ("window_ratio", ctypes.c_float),
                 ("window", ctypes.c_int32), ("wdtw_g", ctypes.c_float), ("wdtw_wmax", ctypes.c_float),
                 ("erp_gap", ctypes.c_float), ("msm_c", ctypes.c_float), ("twe_nu", ctypes.c_float),
-                ("twe_lambda", ctypes.c_float), ("lb", ctypes.c_int32), ("prune", ctypes.c_int32)]
+                ("twe_lambda", ctypes.c_float), ("lb", ctypes.c_int32), ("prune", ctypes.c_int32),
+                ("derivative", ctypes.c_int32)]
 
 
 class eap_series_set(ctypes.Structure):
@@ -116,7 +117,7 @@ def _check(rc: int, where: str):
 def params(kind, **kw) -> eap_params:
     """Parameter block with the distance's defaults, overridden by keywords
     (cost, window_ratio, window, wdtw_g, wdtw_wmax, erp_gap, msm_c, twe_nu,
-    twe_lambda, lb, prune)."""
+    twe_lambda, lb, prune, derivative)."""
     k = KINDS[kind] if isinstance(kind, str) else int(kind)
     p = eap_params()
     load().eap_params_default(ctypes.byref(p), k)

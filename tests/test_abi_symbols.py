@@ -51,3 +51,17 @@ def test_strerror_and_defaults_without_a_gpu():
     assert abs(p.twe_nu - 0.001) < 1e-9 and p.twe_lambda == 1.0 and p.prune == 1
     p = eap.params("cdtw")
     assert abs(p.window_ratio - 0.1) < 1e-7 and p.window == -1
+
+
+def test_params_layout_matches_the_header():
+    # eap_params_default writes exactly sizeof(eap_params) bytes: the ctypes
+    # mirror must have the same size, and the derivative flag defaults to 0.
+    from paper_2102_05221_gb300 import eap
+    lib = eap.load()
+    n = ctypes.sizeof(eap.eap_params)
+    buf = (ctypes.c_uint8 * (n + 16))(*([0xAB] * (n + 16)))
+    lib.eap_params_default(ctypes.cast(buf, ctypes.POINTER(eap.eap_params)), 0)
+    assert bytes(buf[n:]) == b"\xab" * 16
+    p = eap.eap_params.from_buffer_copy(bytes(buf[:n]))
+    assert p.derivative == 0 and p.prune == 1 and p.kind == 0
+    assert eap.params("msm", derivative=1).derivative == 1

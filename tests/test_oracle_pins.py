@@ -338,3 +338,87 @@ def test_msm_hand_evaluated_example():
     p = O.make_params("msm", msm_c=0.5)
     assert O.distance(p, [0.0, 3.0], [1.0, 2.0]) == 2.0
     assert O.distance(p, [0.0, 3.0], [1.0]) == 1.0 + 0.5 + 2.0
+
+
+# ---------------------------------------------------------------------------
+# Derivative distances (Section 2.3: DDTW and the other derivative variants
+# apply the distance to the first-derivative series, after Keogh & Pazzani).
+
+def test_derivative_hand_values():
+    # x = 0 1 3 6: interior estimates ((1-0) + (3-0)/2)/2 = 1.25 and
+    # ((3-1) + (6-1)/2)/2 = 2.25; the ends copy them.  Against a constant series
+    # (derivative 0) every alignment covers each row, so the diagonal is optimal.
+    x = [0.0, 1.0, 3.0, 6.0]
+    z = [5.0, 5.0, 5.0, 5.0]
+    assert O.distance(O.make_params("dtw", derivative=1), x, z) == 2 * 1.25 ** 2 + 2 * 2.25 ** 2
+    assert O.distance(O.make_params("dtw", cost=O.COST_ABS, derivative=1), x, z) == 7.0
+    # Without the derivative the same pair is far apart.
+    assert O.distance(O.make_params("dtw"), x, z) != 13.25
+
+
+@pytest.mark.parametrize("kind,cost,expect", [("dtw", 0, 16 * 0.0625), ("cdtw", 0, 16 * 0.0625),
+                                              ("erp", 1, 16 * 0.25), ("twe", 1, 0.25 + 15 * 0.5)])
+def test_derivative_of_lines_is_constant_slope(kind, cost, expect):
+    # Lines of slope 1/2 and 1/4 have constant derivatives 1/2 and 1/4.
+    # DTW/CDTW: 16 diagonal cells of (1/4)^2.  ERP (gap 0): 16 matches of 1/4
+    # beat 32 gap steps.  TWE (nu, lambda large): the diagonal costs
+    # |1/2-1/4| + |0-0| on the first step and 2 * 1/4 on each later one.
+    x = [0.5 * i for i in range(16)]
+    y = [0.25 * i - 3.0 for i in range(16)]
+    p = O.make_params(kind, cost=cost, window=0 if kind == "cdtw" else -1, erp_gap=0.0,
+                      twe_nu=1.0, twe_lambda=1.0, derivative=1)
+    assert O.distance(p, x, y) == expect
+
+
+def test_derivative_of_one_or_two_points_is_zero():
+    rng = np.random.default_rng(5)
+    for kind in KINDS:
+        # Unequal lengths need a split (MSM) or a deletion (TWE), which costs even on zeros.
+        for la, lb in [(1, 1), (2, 2)] + ([(1, 2)] if kind not in ("msm", "twe") else []):
+            a = rng.normal(size=la).astype(np.float32)
+            b = rng.normal(size=lb).astype(np.float32)
+            assert O.distance(O.make_params(kind, derivative=1, erp_gap=0.0), a, b) == 0.0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_derivative_distance_ignores_offsets(kind):
+    # Values on a 1/8 grid keep x + 3 exact in float32, so the derivatives agree exactly.
+    rng = np.random.default_rng(17 + KINDS.index(kind))
+    for L in (3, 9, 40):
+        x = (rng.integers(-16, 16, L) / 8.0).astype(np.float32)
+        assert O.distance(O.make_params(kind, derivative=1), x, x + np.float32(3.0)) == 0.0
+        assert O.eapruned(O.make_params(kind, derivative=1), x, x + np.float32(3.0), 0.0)[0] == 0.0
+
+
+def _keogh_pazzani(x):
+    x = [float(v) for v in x]
+    n = len(x)
+    if n <= 2:
+        return [0.0] * n
+    d = [0.0] * n
+    for i in range(1, n - 1):
+        d[i] = ((x[i] - x[i - 1]) + (x[i + 1] - x[i - 1]) / 2.0) / 2.0
+    d[0], d[-1] = d[1], d[-2]
+    return d
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_derivative_oracle_equals_bruteforce(kind):
+    """The derivative variant is the brute-force minimum over paths of the derivative series."""
+    rng = np.random.default_rng(40 + KINDS.index(kind))
+    cost = 0 if kind in ("dtw", "cdtw", "wdtw") else 1
+    for ls, lt in [(3, 3), (4, 6), (6, 4), (6, 6)]:
+        s = rng.uniform(-2, 2, ls).astype(np.float32)
+        t = rng.uniform(-2, 2, lt).astype(np.float32)
+        windows = [None] if kind not in ("cdtw", "erp") else [None, 1, 2]
+        for w in windows:
+            p = O.make_params(kind, cost=cost, window=-1 if w is None else w, erp_gap=0.3,
+                              msm_c=0.5, twe_nu=0.25, twe_lambda=0.5, wdtw_g=0.4, derivative=1)
+            bf = brute.brute_distance(kind, _keogh_pazzani(s), _keogh_pazzani(t), cost,
+                                      gap=float(np.float32(0.3)), msm_c=0.5, nu=0.25, lam=0.5,
+                                      g=float(np.float32(0.4)), **_bf_kwargs(kind, w))
+            assert O.distance(p, s, t) == bf, (kind, ls, lt, w)
+            # Alg. 5 on the derivative series: exact at cut-off D, +inf below it.
+            if math.isfinite(bf):
+                assert O.eapruned(p, s, t, bf)[0] == bf
+                assert O.eapruned(p, s, t, bf * 0.999)[0] == math.inf
