@@ -82,6 +82,9 @@ def _load():
             lib.orc_eapruned.restype = ctypes.c_double
             lib.orc_eapruned.argtypes = [P(OrcParams), f32p, ctypes.c_int, f32p, ctypes.c_int,
                                          ctypes.c_double, i64p]
+            lib.orc_eabase.restype = ctypes.c_double
+            lib.orc_eabase.argtypes = [P(OrcParams), f32p, ctypes.c_int, f32p, ctypes.c_int,
+                                       ctypes.c_double, i64p]
             lib.orc_nn1.restype = ctypes.c_int
             lib.orc_nn1.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int,
                                     f32p, i64p, i32p, ctypes.c_int, i32p, f64p, ctypes.c_int]
@@ -119,6 +122,16 @@ def eapruned(params: OrcParams, s, t, cutoff: float):
     cells = ctypes.c_int64(0)
     d = _load().orc_eapruned(ctypes.byref(params), _ptr(s, ctypes.c_float), len(s),
                              _ptr(t, ctypes.c_float), len(t), float(cutoff), ctypes.byref(cells))
+    return d, int(cells.value)
+
+
+def eabase(params: OrcParams, s, t, cutoff: float):
+    """Algorithm 4 (EABase): returns (D, or +inf if abandoned on a row
+    minimum above the cut-off; number of computed cells)."""
+    s, t = _f32(s), _f32(t)
+    cells = ctypes.c_int64(0)
+    d = _load().orc_eabase(ctypes.byref(params), _ptr(s, ctypes.c_float), len(s),
+                           _ptr(t, ctypes.c_float), len(t), float(cutoff), ctypes.byref(cells))
     return d, int(cells.value)
 
 

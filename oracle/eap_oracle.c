@@ -19,6 +19,8 @@
  *   orc_eapruned   Algorithm 5 (generic EAPruned) step by step in the paper's
  *                  stages, with a counter of computed cells (used to pin the
  *                  paper's worked-example counts, Section 3.2).
+ *   orc_eabase     Algorithm 4 (Base with a window and the usual early
+ *                  abandoning on the row minimum), with a cell counter.
  *   orc_nn1        Algorithm 1 (NN search) over candidates in index order with
  *                  the strict "<" update; threads split the queries.
  *   orc_pairwise   the full distance matrix (the exact values that prune-only
@@ -262,18 +264,14 @@ static double o_altcol(const o_ctx* x, int i, int j) {
     return NAN;
 }
 
-double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* tf, int lt,
-                    double cutoff, int64_t* cells) {
-    int64_t n = 0;
-    if (ls <= 0 || lt <= 0) return NAN;
-    const long w = o_window(p, ls, lt);
-    /* co: shortest series on the columns; li: longest on the rows. */
+/* Series of Alg. 4 / Alg. 5 in double, 1-indexed: *r = the longest ("li",
+ * rows), *c = the shortest ("co", columns), derivative applied if asked. */
+static void o_setup(const orc_params* p, const float* sf, int ls, const float* tf, int lt,
+                    double** r_out, double** c_out, int* Lli_out, int* Lco_out) {
     const float* cof = lt <= ls ? tf : sf;
     const float* lif = lt <= ls ? sf : tf;
     const int Lco = lt <= ls ? lt : ls;
     const int Lli = lt <= ls ? ls : lt;
-    if (cells) *cells = 0;
-    if (w < (long)(Lli - Lco)) return OINF;
     double* r = (double*)calloc((size_t)Lli + 1, sizeof(double));
     double* c = (double*)calloc((size_t)Lco + 1, sizeof(double));
     for (int i = 1; i <= Lli; i++) r[i] = (double)lif[i - 1];
@@ -287,6 +285,22 @@ double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* t
         for (int j = 1; j <= Lco; j++) c[j] = dc[j - 1];
         free(dr); free(dc);
     }
+    *r_out = r; *c_out = c; *Lli_out = Lli; *Lco_out = Lco;
+}
+
+double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* tf, int lt,
+                    double cutoff, int64_t* cells) {
+    int64_t n = 0;
+    if (ls <= 0 || lt <= 0) return NAN;
+    const long w = o_window(p, ls, lt);
+    if (cells) *cells = 0;
+    /* co: shortest series on the columns; li: longest on the rows. */
+    const int Lco = lt <= ls ? lt : ls;
+    const int Lli = lt <= ls ? ls : lt;
+    if (w < (long)(Lli - Lco)) return OINF;
+    double *r, *c;
+    int Lli_, Lco_;
+    o_setup(p, sf, ls, tf, lt, &r, &c, &Lli_, &Lco_);
     o_ctx x = {p, r, c, Lli};
     double* prev = (double*)malloc(((size_t)Lco + 1) * sizeof(double));
     double* curr = (double*)malloc(((size_t)Lco + 1) * sizeof(double));
@@ -329,9 +343,13 @@ double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* t
             n++;
             if (curr[j] <= cutoff) next_pruning_point = j + 1;
         }
+        /* A computed vertical border cell (ERP, column 0 of this row) that is
+         * <= cut-off belongs to the row's live cells: a path can run down the
+         * border and enter the interior in a later row. */
+        const int border_live = (j_start == 1) && curr[0] <= cutoff;
         /* Stage 4: at the pruning point. */
         if (j <= j_stop) {
-            if (j == next_start) {
+            if (j == next_start && !border_live) {
                 curr[j] = prev[j - 1] + o_canon(&x, i, j);
                 n++;
                 if (curr[j] <= cutoff) next_pruning_point = j + 1;
@@ -342,7 +360,7 @@ double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* t
                 if (curr[j] <= cutoff) next_pruning_point = j + 1;
             }
             j++;
-        } else if (j == next_start) {
+        } else if (j == next_start && !border_live) {
             abandoned = 1;
             break;
         }
@@ -360,6 +378,61 @@ double orc_eapruned(const orc_params* p, const float* sf, int ls, const float* t
         result = (pruning_point > Lco) ? curr[Lco] : OINF;
         if (!(result <= cutoff)) result = OINF;
     }
+    if (cells) *cells = n;
+    free(r); free(c); free(prev); free(curr);
+    return result;
+}
+
+/* ------------------------------------------------------------------------
+ * Algorithm 4: the Base DP with a window and the usual early abandoning
+ * (EABase).  Rows are the longest series, columns the shortest; after each
+ * row, the computation is abandoned (+inf) when the smallest value of the
+ * row exceeds the cut-off.  Otherwise M(L_li, L_co) is returned, which may
+ * itself exceed the cut-off.  The row minimum includes the row's vertical
+ * border cell while the window covers column 0 (ERP's computed border): a
+ * path can run down that border, so leaving it out could abandon a distance
+ * that is below the cut-off.  *cells counts the interior cells computed.
+ * ------------------------------------------------------------------------ */
+double orc_eabase(const orc_params* p, const float* sf, int ls, const float* tf, int lt,
+                  double cutoff, int64_t* cells) {
+    int64_t n = 0;
+    if (ls <= 0 || lt <= 0) return NAN;
+    const long w = o_window(p, ls, lt);
+    if (cells) *cells = 0;
+    const int Lco = lt <= ls ? lt : ls;
+    const int Lli = lt <= ls ? ls : lt;
+    if (w < (long)(Lli - Lco)) return OINF;
+    double *r, *c;
+    int Lli_, Lco_;
+    o_setup(p, sf, ls, tf, lt, &r, &c, &Lli_, &Lco_);
+    o_ctx x = {p, r, c, Lli};
+    double* prev = (double*)malloc(((size_t)Lco + 1) * sizeof(double));
+    double* curr = (double*)malloc(((size_t)Lco + 1) * sizeof(double));
+    for (int j = 0; j <= Lco; j++) prev[j] = curr[j] = OINF;
+    curr[0] = 0.0;
+    const long hb_end = w + 1 < (long)Lco ? w + 1 : (long)Lco;
+    for (long j = 1; j <= hb_end; j++)
+        curr[j] = (p->kind == O_ERP) ? curr[j - 1] + o_cost(p->cost, p->erp_gap, c[j]) : OINF;
+    double result = OINF;
+    int abandoned = 0;
+    for (long i = 1; i <= Lli; i++) {
+        double* tmp = prev; prev = curr; curr = tmp;
+        const long j_start = (i - w) > 1 ? (i - w) : 1;
+        const long j_stop = (i + w) < (long)Lco ? (i + w) : (long)Lco;
+        if (j_start == 1)
+            curr[0] = (p->kind == O_ERP) ? prev[0] + o_cost(p->cost, r[i], p->erp_gap) : OINF;
+        else
+            curr[j_start - 1] = OINF;
+        double minv = (j_start == 1) ? curr[0] : OINF;
+        for (long j = j_start; j <= j_stop; j++) {
+            curr[j] = o_min3(prev[j - 1] + o_canon(&x, i, j), prev[j] + o_altrow(&x, i, j),
+                             curr[j - 1] + o_altcol(&x, i, j));
+            n++;
+            if (curr[j] < minv) minv = curr[j];
+        }
+        if (minv > cutoff) { abandoned = 1; break; }
+    }
+    if (!abandoned) result = curr[Lco];
     if (cells) *cells = n;
     free(r); free(c); free(prev); free(curr);
     return result;

@@ -29,6 +29,8 @@ def _read_golden(name):
             parts = line.split()
             if parts[0] == "EAPRUNED_CUTOFF":
                 extra.append((float(parts[1]), float(parts[3]), int(parts[5])))
+            elif parts[0] == "EABASE_CUTOFF":
+                rows.setdefault("EABASE", []).append((float(parts[1]), float(parts[3]), int(parts[5])))
             else:
                 rows[parts[0]] = [float(x) for x in parts[1:]]
     return rows, extra
@@ -422,3 +424,64 @@ def test_derivative_oracle_equals_bruteforce(kind):
             if math.isfinite(bf):
                 assert O.eapruned(p, s, t, bf)[0] == bf
                 assert O.eapruned(p, s, t, bf * 0.999)[0] == math.inf
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4 (EABase: Base with the usual early abandoning on the row minimum).
+
+def test_eabase_worked_example_cell_counts():
+    g, _ = _read_golden("dtw_worked_example.txt")
+    S, T = g["S"], g["T"]
+    for cutoff, result, cells in g["EABASE"]:
+        d, n = O.eabase(O.make_params("dtw"), S, T, cutoff)
+        assert (d, n) == (result, cells), (cutoff, d, n)
+    assert O.eabase(O.make_params("dtw"), S, T, math.inf) == (9.0, 36)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_eabase_contract_and_bruteforce(kind):
+    """D exactly when D <= cut-off; when D > cut-off, D or +inf; and the
+    brute-force minimum over paths when no cut-off is given."""
+    rng = np.random.default_rng(70 + KINDS.index(kind))
+    cost = 0 if kind in ("dtw", "cdtw", "wdtw") else 1
+    for ls, lt in [(1, 1), (3, 5), (5, 3), (6, 6)]:
+        s = rng.uniform(-2, 2, ls).astype(np.float32)
+        t = rng.uniform(-2, 2, lt).astype(np.float32)
+        for w in ([None] if kind not in ("cdtw", "erp") else [None, 1, 2]):
+            p = O.make_params(kind, cost=cost, window=-1 if w is None else w, erp_gap=0.3,
+                              msm_c=0.5, twe_nu=0.25, twe_lambda=0.5, wdtw_g=0.4)
+            bf = brute.brute_distance(kind, s, t, cost, gap=float(np.float32(0.3)), msm_c=0.5, nu=0.25,
+                                      lam=0.5, g=float(np.float32(0.4)), **_bf_kwargs(kind, w))
+            assert O.eabase(p, s, t, math.inf)[0] == bf
+            if not math.isfinite(bf):
+                continue
+            for cut in (bf, bf * 1.5, bf * 0.999, bf * 0.5, 0.0):
+                d, _ = O.eabase(p, s, t, cut)
+                if bf <= cut:
+                    assert d == bf, (kind, ls, lt, w, cut, d, bf)
+                else:
+                    assert d == bf or d == math.inf, (kind, ls, lt, w, cut, d, bf)
+
+
+def test_eabase_abandons_on_a_row_above_the_cutoff():
+    # A cut-off below every cell of the first row abandons after that row;
+    # rows never exceed L_co cells.
+    x = _walks(2, 50, 9)
+    s, t = x[0], x[1] + np.float32(10.0)
+    d, n = O.eabase(O.make_params("dtw"), s, t, 1.0)
+    assert d == math.inf and n == 50
+    # A cut-off at D never abandons and computes the whole matrix.
+    D = O.distance(O.make_params("dtw"), s, t)
+    assert O.eabase(O.make_params("dtw"), s, t, D) == (D, 2500)
+
+
+def test_eabase_erp_row_minimum_includes_the_vertical_border():
+    # S = (0, 0, 0, 5), T = (5), gap 0: the optimal path runs down the border
+    # (cost 0) and matches 5 with 5 last, so ERP = 0, while the first row's
+    # only interior cell costs 5.  A row minimum without the border cell would
+    # abandon this pair at cut-off 4.
+    p = O.make_params("erp", cost=O.COST_ABS, erp_gap=0.0)
+    s, t = [0.0, 0.0, 0.0, 5.0], [5.0]
+    assert O.distance(p, s, t) == 0.0
+    assert O.eabase(p, s, t, 4.0)[0] == 0.0
+    assert O.eapruned(p, s, t, 4.0)[0] == 0.0
