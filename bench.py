@@ -222,7 +222,7 @@ def main():
     ap.add_argument("--mode", default="per-distance", choices=["per-distance", "batch"],
                     help="per-distance: one eap_nn1 call per distance; batch: all six in one eap_nn1_batch launch")
     ap.add_argument("--workload", default="nn1_512",
-                    choices=["nn1_512", "unpruned_512", "allpairs_4096", "uneven_64", "serving"],
+                    choices=["nn1_512", "unpruned_512", "modes_512", "allpairs_4096", "uneven_64", "serving"],
                     help="nn1_512 is the benchmark; the others measure the remaining workloads")
     args = ap.parse_args()
     kinds = [k for k in args.kinds.split(",") if k]
@@ -471,6 +471,55 @@ def workload_unpruned_512(args):
             "roofline_peak_ops": peak}
 
 
+def workload_modes_512(args):
+    """Base, Prune, EABase and EAPruned 1-NN (the four implementations of the
+    paper's NN experiment, Section 4.1) on the 1000 x 1000 x 512 workload:
+    whole eap_nn1 calls (upper bounds, sort and DP) timed with CUDA events,
+    L2 flushed before each call."""
+    import statistics
+
+    import torch
+
+    from paper_2102_05221_gb300 import eap
+    ds = make_inputs(0)
+    R, Q = eap.SeriesSet.from_matrix(ds.train), eap.SeriesSet.from_matrix(ds.test)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    modes = {"base": 0, "prune": 3, "eabase": 2, "eapruned": 1}
+    out, total = {}, {m: 0.0 for m in modes}
+    for k in args.kinds.split(","):
+        row = {}
+        for name, m in modes.items():
+            p = eap.params(k, prune=m, **KIND_PARAMS[k])
+            for _ in range(max(1, args.warmup)):
+                eap.eap_nn1(p, Q, R)
+            ms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                ms.append(_sync_time(lambda: eap.eap_nn1(p, Q, R)))
+            _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
+            t = statistics.median(ms)
+            total[name] += t
+            row[name] = {"ms": t, "queries_per_s": Q.count / (t / 1e3),
+                         "cells_computed_over_effective": st["cells_computed"] / max(1, st["cells_effective"]),
+                         "pairs_abandoned": st["pairs_abandoned"]}
+        e = row["eapruned"]["ms"]
+        row["eapruned_speedup"] = {"vs_base": row["base"]["ms"] / e, "vs_eabase": row["eabase"]["ms"] / e,
+                                   "vs_prune": row["prune"]["ms"] / e}
+        out[k] = row
+    e = total["eapruned"]
+    return {"metric": "1-NN time per implementation: Base / Prune / EABase / EAPruned, 1000 x 1000 x 512",
+            "value": total["base"] / e, "unit": "x (EAPruned speed-up over Base, six distances summed)",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "nn1_modes_1000x1000_L512", "steps": args.steps,
+                       "l2": "flushed before each call (512 MiB write)"},
+            "total_ms": total,
+            "speedup_all": {"vs_base": total["base"] / e, "vs_eabase": total["eabase"] / e,
+                            "vs_prune": total["prune"] / e},
+            "paper_cpu_context": {"vs_base": 7.61, "vs_eabase": 2.86,
+                                  "note": "UCR archive, 85 datasets, one Opteron core (Section 4.1)"},
+            "per_distance": out}
+
+
 def workload_allpairs_4096(args):
     """256 random walks of length 4096: full DTW and MSM matrices, prune-only."""
     import torch
@@ -647,7 +696,8 @@ def run_other_workload(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     from paper_2102_05221_gb300 import eap
     eap.load()
-    fn = {"unpruned_512": workload_unpruned_512, "allpairs_4096": workload_allpairs_4096,
+    fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512,
+          "allpairs_4096": workload_allpairs_4096,
           "uneven_64": workload_uneven_64, "serving": workload_serving}[args.workload]
     line = fn(args)
     line.setdefault("n_gpus", 1)

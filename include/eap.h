@@ -73,7 +73,17 @@ typedef struct {
     float   twe_nu;        /* TWE stiffness nu >= 0 */
     float   twe_lambda;    /* TWE penalty lambda >= 0 */
     int32_t lb;            /* eap_lb */
-    int32_t prune;         /* 1 = EAPruned (Alg. 5 semantics); 0 = Base (Alg. 3: no pruning, no abandoning) */
+    int32_t prune;         /* 1 = EAPruned (Alg. 5 semantics: D if D <= cut-off, else +inf);
+                            * 0 = Base (Alg. 3: no pruning, no abandoning);
+                            * 2 = EABase (Alg. 4: every cell until the computation is abandoned; returns
+                            *     D, or +inf when a cut of the cost matrix -- on the device, the
+                            *     wavefront's staircase of newest cells -- lies entirely above the
+                            *     cut-off; +inf only if D > cut-off, and a returned D may exceed it).
+                            *     Warp mapping only; not accepted by eap_nn1_batch;
+                            * 3 = Prune (pruning only: EAPruned with each pair's own diagonal-path cost as
+                            *     cut-off, never abandoning; every distance exact).  eap_nn1 family and
+                            *     serving only (eap_pairs: EAP_EINVAL; all-pairs: eap_pairwise with
+                            *     EAP_PRUNE_ONLY). */
     int32_t derivative;    /* 1 = derivative variant (DDTW, DCDTW, DWDTW, ...; Section 2.3): the distance of
                             * the first-derivative series d_i = ((x_i - x_{i-1}) + (x_{i+1} - x_{i-1})/2)/2
                             * (Keogh & Pazzani's estimate; the end points copy their neighbour, series of

@@ -275,7 +275,7 @@ int validate_params(const eap_params* p) {
     if (!p) return EAP_EINVAL;
     if (p->kind < EAP_DTW || p->kind > EAP_TWE) return EAP_EINVAL;
     if (p->cost != EAP_COST_DEFAULT && p->cost != EAP_COST_SQ && p->cost != EAP_COST_ABS) return EAP_EINVAL;
-    if (p->prune != 0 && p->prune != 1) return EAP_EINVAL;
+    if (p->prune < 0 || p->prune > 3) return EAP_EINVAL;
     if (p->derivative != 0 && p->derivative != 1) return EAP_EINVAL;
     if (p->lb < EAP_LB_NONE || p->lb > EAP_LB_KEOGH2) return EAP_EINVAL;
     if (!finite_f(p->window_ratio)) return EAP_EINVAL;
@@ -338,8 +338,9 @@ int length_bucket(int len);
 std::mutex g_map_mu;
 int g_map[6][2][16] = {};   // [kind][cost][bucket] -> 0 untuned, 1 warp, 2 CTA (set by the autotuner)
 
-int choose_cta(int kind, int cost, int max_rows, int max_cols) {
+int choose_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
     if (kind == EAP_CDTW || kind == EAP_ERP) return 0;
+    if (prune == kPmEA) return 0;   // EABase runs on the warp mapping only
     const char* e = std::getenv("EAP_MAP");
     if (e && std::strcmp(e, "warp") == 0) return 0;
     if (e && std::strcmp(e, "cta") == 0) return 1;
@@ -357,12 +358,13 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
         const int w = std::atoi(e);
         if (w == 4 || w == 8 || w == 16) return w;
     }
-    if (prune && kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
+    if (prune == kPmPruned && kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         const int t = g_tune[kind][cost][length_bucket(max_cols)];
         if (t) return t;
     }
-    if (!prune) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
+    // Base and EABase compute (nearly) every cell: wide strips.
+    if (prune != kPmPruned) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
     if (kind == EAP_TWE && max_cols > 128) return 8;
     return 4;
 }
@@ -562,12 +564,15 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.kp.wdtw_w = d_wt;
     c.kind = p->kind;
     c.cost = cost;
-    c.prune = prune ? 1 : 0;
+    // Prune (3) runs the EAPruned kernel with each pair's own diagonal bound as cut-off.
+    const bool own_cut = p->prune == 3;
+    c.prune = own_cut ? kPmPruned : p->prune;
+    c.job.cut = own_cut ? d_ub : nullptr;
     c.W = choose_w(p->kind, cost, mr, c.prune);
     c.sms = sms;
     c.max_rows = mq;
     c.max_cols = mr;
-    c.cta = choose_cta(p->kind, cost, mq, mr);
+    c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -820,7 +825,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.sms = sms;
         c.max_rows = mx;
         c.max_cols = mx;
-        c.cta = choose_cta(p->kind, cost, mx, mx);
+        c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -858,6 +863,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     if (n == 0) return EAP_OK;
     if (!ia || !ib || !out || (p->prune && !cutoff) || a->count == 0 || b->count == 0) return EAP_EINVAL;
+    if (p->prune == 3) return EAP_EINVAL;   // pruning-only with own bounds: eap_pairwise(EAP_PRUNE_ONLY) / eap_nn1
     const int sms = device_sms();
     if (sms <= 0) return EAP_EDEVICE;
     const bool erp = p->kind == EAP_ERP, wdtw = p->kind == EAP_WDTW;
@@ -903,12 +909,12 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.kp.wdtw_w = L.wt;
     c.kind = p->kind;
     c.cost = cost;
-    c.prune = p->prune ? 1 : 0;
+    c.prune = p->prune;
     c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
     c.max_cols = mb;
-    c.cta = choose_cta(p->kind, cost, ma, mb);
+    c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1003,6 +1009,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     if (n == 0) return EAP_OK;
     if (!ia || !ib || !out || (p->prune && !cutoff) || a->count == 0 || b->count == 0) return EAP_EINVAL;
+    if (p->prune == 3) return EAP_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int sms = device_sms();
     if (sms <= 0) return EAP_EDEVICE;
@@ -1070,7 +1077,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.kp.wdtw_w = d_wt;
     c.kind = p->kind;
     c.cost = cost;
-    c.prune = p->prune ? 1 : 0;
+    c.prune = p->prune;
     c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;

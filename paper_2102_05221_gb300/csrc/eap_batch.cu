@@ -103,17 +103,17 @@ template <int W>
 __device__ float pair_by_fn(int fn, const PairIn& in, float* bnd, const KParams& kp, unsigned long long& cells,
                             bool& ab) {
     switch (fn) {
-        case kFnDtwSq: return warp_pair<FDtw<0>, W, true, false>(in, bnd, kp, cells, ab);
-        case kFnDtwAbs: return warp_pair<FDtw<1>, W, true, false>(in, bnd, kp, cells, ab);
-        case kFnCdtwSq: return warp_pair<FDtw<0>, W, true, true>(in, bnd, kp, cells, ab);
-        case kFnCdtwAbs: return warp_pair<FDtw<1>, W, true, true>(in, bnd, kp, cells, ab);
-        case kFnWdtwSq: return warp_pair<FWdtw<0>, W, true, false>(in, bnd, kp, cells, ab);
-        case kFnWdtwAbs: return warp_pair<FWdtw<1>, W, true, false>(in, bnd, kp, cells, ab);
-        case kFnErpSq: return warp_pair<FErp<0>, W, true, true>(in, bnd, kp, cells, ab);
-        case kFnErpAbs: return warp_pair<FErp<1>, W, true, true>(in, bnd, kp, cells, ab);
-        case kFnMsm: return warp_pair<FMsm, W, true, false>(in, bnd, kp, cells, ab);
-        case kFnTweSq: return warp_pair<FTwe<0>, W, true, false>(in, bnd, kp, cells, ab);
-        default: return warp_pair<FTwe<1>, W, true, false>(in, bnd, kp, cells, ab);
+        case kFnDtwSq: return warp_pair<FDtw<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        case kFnDtwAbs: return warp_pair<FDtw<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        case kFnCdtwSq: return warp_pair<FDtw<0>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
+        case kFnCdtwAbs: return warp_pair<FDtw<1>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
+        case kFnWdtwSq: return warp_pair<FWdtw<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        case kFnWdtwAbs: return warp_pair<FWdtw<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        case kFnErpSq: return warp_pair<FErp<0>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
+        case kFnErpAbs: return warp_pair<FErp<1>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
+        case kFnMsm: return warp_pair<FMsm, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        case kFnTweSq: return warp_pair<FTwe<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
+        default: return warp_pair<FTwe<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
     }
 }
 

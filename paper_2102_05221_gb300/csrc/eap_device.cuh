@@ -310,18 +310,28 @@ __device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, in
     }
 }
 
-// Returns D(A,B) if it is <= in.cut (PRUNE) or always (Base), else +inf.
+// Modes of the pair DP: Base (Alg. 3, every cell), EAPruned (Alg. 5) and
+// EABase (Alg. 4: every cell until a cut of the lattice exceeds the cut-off).
+constexpr int kPmBase = 0, kPmPruned = 1, kPmEA = 2;
+
+// Returns D(A,B) if it is <= in.cut (EAPruned) or always (Base); EABase
+// returns D or +inf, +inf only when D > in.cut.
 // bnd: this warp's shared-memory column of La+1 floats.  cells: per-lane
 // running count of evaluated cells.
-template <class F, int W, bool PRUNE, bool WIN>
+template <class F, int W, int PM, bool WIN>
 __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KParams& kp,
                            unsigned long long& cells, bool& abandoned) {
+    constexpr bool PRUNE = PM == kPmPruned;
+    constexpr bool EA = PM == kPmEA;
     const int lane = threadIdx.x & 31;
     const int La = in.La, Lb = in.Lb, w = in.w;
     constexpr int P = 32 * W;
     const int npan = (Lb + P - 1) / P;
-    float cut = PRUNE ? in.cut : EAP_FINF;
+    float cut = PRUNE ? in.cut : EAP_FINF;     // pruning threshold (EAPruned)
+    float eacut = EA ? in.cut : EAP_FINF;      // abandoning threshold (EABase)
     abandoned = false;
+    // EABase: last row of the boundary column this panel reads whose value is <= eacut.
+    int ea_bl = 0;
 
     // Left boundary of panel 0 is the vertical border M(r, 0): rows [blo, bhi]
     // of bnd hold readable values, everything else is +inf.
@@ -334,6 +344,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             const float x = r <= vmax ? __ldg(in.bA + r - 1) : EAP_FINF;
             if (r <= vmax) bnd[r] = x;
             live += __popc(__ballot_sync(EAP_FULL, r <= vmax && x <= cut));
+            if (EA) ea_bl += __popc(__ballot_sync(EAP_FULL, r <= vmax && x <= eacut));
         }
         if (live > 0) { blo = 1; bhi = live; }   // the border is monotone: live rows are a prefix
     }
@@ -343,14 +354,19 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         const int cf = p * P + 1;
         const int cl = min(cf + P - 1, Lb);
         const bool last = (p == npan - 1);
-        if (PRUNE && in.cut_src) {
+        if ((PRUNE || EA) && in.cut_src) {
             // One lane reads the shared best-so-far and broadcasts it, so the
             // whole warp takes the same pruning decisions.
             unsigned long long cv = 0;
             if (lane == 0) cv = *(volatile const unsigned long long*)in.cut_src;
             cv = __shfl_sync(EAP_FULL, cv, 0);
-            cut = fminf(cut, __uint_as_float((unsigned)(cv >> 32)));
+            const float c2 = __uint_as_float((unsigned)(cv >> 32));
+            if (PRUNE) cut = fminf(cut, c2);
+            else eacut = fminf(eacut, c2);
         }
+        // EABase: a top-border cell right of this panel at or below the
+        // cut-off (ERP; the border increases, so the first one decides).
+        const bool ea_top_beyond = EA && !last && hborder<F>(in, cl + 1) <= eacut;
         // Rows of this panel that can hold a live cell start at row 1 if the
         // top border left of / inside it is live, else at the first live row
         // of the left boundary (pruning from the left).
@@ -362,6 +378,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         if (r0 > r1) {
             if (last) return EAP_FINF;
             blo = 1; bhi = 0;
+            ea_bl = 0;
             continue;
         }
 
@@ -404,6 +421,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         float sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
         float s_next = __ldg(in.A + r0 - 1);
         const int nsteps = r1 - r0 + 32;
+        bool ea_handed = false;   // EABase: lane 31 handed a value <= eacut to the next panel
 
         // One step of the skewed wavefront; ACTIVE_CHECK for the ramps, where
         // some lanes have not started or have finished.
@@ -422,7 +440,10 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                 strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                 sp = s;
                 dg = x;
-                if (st31) bnd[row] = v[W - 1];
+                if (st31) {
+                    bnd[row] = v[W - 1];
+                    if (EA) ea_handed = ea_handed || v[W - 1] <= eacut;
+                }
             }
         };
         // Dead-frontier vote: every cell a later row of this panel could
@@ -440,13 +461,34 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             }
             return __all_sync(EAP_FULL, dead);
         };
+        // EABase: every cell of the current cut of the lattice exceeds the
+        // cut-off.  The cut is the staircase of each lane's newest strip
+        // values and left input (a lane that has finished the panel keeps
+        // its last row, which holds M(L_A, L_B) once the pair is done), the
+        // boundary rows lane 0 has not consumed, the rows already handed to
+        // the next panel and the top border right of the panel; every
+        // alignment path crosses it, so D > cut-off.
+        auto ea_dead = [&](int t) -> bool {
+            const int row = r0 + t - lane;
+            bool dead = !ea_top_beyond && !ea_handed;
+            if (dead && !lane_out) {
+                float m = dg;
+#pragma unroll
+                for (int u = 0; u < W; ++u) m = fminf(m, v[u]);
+                dead = m > eacut;
+            }
+            if (lane == 0 && row < ea_bl) dead = false;
+            return __all_sync(EAP_FULL, dead);
+        };
         int done = nsteps;   // steps executed
         int t = 0;
         bool stop = false;
         const int ramp_end = min(31, nsteps);
+        bool ea_ab = false;
         for (; t < ramp_end; ++t) {
             step(t, BoolC<true>{});
             if (PRUNE && (t & 3) == 3 && frontier_dead(t)) { done = t + 1; stop = true; break; }
+            if (EA && (t & 3) == 3 && ea_dead(t)) { done = t + 1; stop = ea_ab = true; break; }
         }
         const int steady_end = r1 - r0 + 1;   // steps [31, steady_end) have every lane active
         if (!stop) {
@@ -459,12 +501,14 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
 #pragma unroll
                 for (int k = 0; k < U; ++k) step(t + k, BoolC<false>{});
                 if (PRUNE && frontier_dead(t + U - 1)) { done = t + U; stop = true; break; }
+                if (EA && ea_dead(t + U - 1)) { done = t + U; stop = ea_ab = true; break; }
             }
         }
         if (!stop) {
             for (; t < nsteps; ++t) {
                 step(t, BoolC<true>{});
                 if (PRUNE && (t & 3) == 3 && frontier_dead(t)) { done = t + 1; break; }
+                if (EA && (t & 3) == 3 && ea_dead(t)) { done = t + 1; ea_ab = true; break; }
             }
         }
         t = done;
@@ -474,6 +518,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             if (lastrow >= r0) cells += (unsigned long long)(lastrow - r0 + 1) * (unsigned)nvalid;
         }
         __syncwarp();
+        if (EA && ea_ab) { abandoned = true; return EAP_FINF; }
         if (last) {
             const int off = Lb - cf;         // offset of column Lb inside the panel
             const int lr = off / W, ur = off % W;
@@ -489,16 +534,24 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         }
         // Live rows of the column handed to the next panel.
         const int wlast = min(r1, r0 + t - 1 - 31);
-        int lo = 0x7fffffff, hi = -1;
+        int lo = 0x7fffffff, hi = -1, ea_hi = 0;
         for (int r = r0 + lane; r <= wlast; r += 32) {
-            if (bnd[r] <= cut) { lo = min(lo, r); hi = max(hi, r); }
+            const float b = bnd[r];
+            if (b <= cut) { lo = min(lo, r); hi = max(hi, r); }
+            if (EA && b <= eacut) ea_hi = max(ea_hi, r);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(EAP_FULL, lo, o));
             hi = max(hi, __shfl_xor_sync(EAP_FULL, hi, o));
+            if (EA) ea_hi = max(ea_hi, __shfl_xor_sync(EAP_FULL, ea_hi, o));
         }
         if (hi < 0) { blo = 1; bhi = 0; } else { blo = lo; bhi = hi; }
+        if (EA) {
+            // The whole handed column (and the top border beyond it) above the cut-off.
+            if (ea_hi == 0 && !ea_top_beyond) { abandoned = true; return EAP_FINF; }
+            ea_bl = ea_hi;
+        }
         __syncwarp();
     }
     return EAP_FINF;   // not reached: the last panel returns

@@ -17,7 +17,7 @@ struct LaunchCtx {
     int kind;            // eap_kind
     int cost;            // resolved: 0 squared, 1 absolute
     int W;               // strip width per lane (4, 8 or 16)
-    int prune;           // 1 EAPruned, 0 Base
+    int prune;           // 1 EAPruned, 0 Base, 2 EABase (eapd::kPm*)
     int sms;             // multiprocessors of the device
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
@@ -70,8 +70,9 @@ int launch_dp_twe(const LaunchCtx& c, bool ub_only);
 template <class F, int W, bool WIN>
 int run_dp(const LaunchCtx& c) {
     using namespace eapd;
-    void (*kern)(const DPJob, const KParams) =
-        c.prune ? dp_kernel<F, W, true, WIN> : dp_kernel<F, W, false, WIN>;
+    void (*kern)(const DPJob, const KParams) = c.prune == kPmPruned ? dp_kernel<F, W, kPmPruned, WIN>
+                                               : c.prune == kPmEA    ? dp_kernel<F, W, kPmEA, WIN>
+                                                                     : dp_kernel<F, W, kPmBase, WIN>;
     const size_t smem = (size_t)kWarpsPerBlock * c.job.bnd_stride * sizeof(float);
     cudaError_t e;
     if (smem > 48 * 1024) {

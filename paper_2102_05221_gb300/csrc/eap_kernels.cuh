@@ -33,7 +33,8 @@ struct DPJob {
     unsigned long long* counter;       // work-queue head
     const int32_t* order;              // nn1: candidates of query q by rank, [A.n x B.n] (null = index order)
     unsigned long long* best;          // nn1: packed (float bits << 32 | index) per query
-    const float* cut;                  // pairwise / pairs: per-item cut-off (null = +inf)
+    const float* cut;                  // pairwise / pairs: per-item cut-off (null = +inf); nn1: the pair's
+                                       // own cut-off [A.n x B.n] instead of the shared best-so-far ("Prune")
     float* out;                        // pairwise: n x n matrix; pairs: n results
     const int32_t* ia;                 // pairs
     const int32_t* ib;
@@ -62,8 +63,9 @@ __device__ __forceinline__ void tri_decode(unsigned long long k, int n, int& i, 
     j = (int)(k - S(ii) + (unsigned long long)ii + 1ULL);
 }
 
-template <class F, int W, bool PRUNE, bool WIN>
+template <class F, int W, int PM, bool WIN>
 __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KParams kp) {
+    constexpr bool CUTS = PM != kPmBase;   // EAPruned and EABase take a cut-off
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
     float* bnd = smem + (threadIdx.x >> 5) * job.bnd_stride;
@@ -81,7 +83,11 @@ __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KPa
             ai = (int)(item - rank * (unsigned)job.A.n);
             bi = job.order ? __ldg(job.order + (size_t)ai * job.B.n + rank) : (int)rank;
             cut_src = job.best + ai;
-            if (PRUNE) {
+            if (CUTS && job.cut) {
+                // Pruning only: the pair's own diagonal-path cost, never the shared best-so-far.
+                cut = __ldg(job.cut + (size_t)ai * job.B.n + bi);
+                cut_src = nullptr;
+            } else if (CUTS) {
                 unsigned long long cv = 0;
                 if (lane == 0) cv = *(volatile const unsigned long long*)cut_src;
                 cv = __shfl_sync(EAP_FULL, cv, 0);   // warp-uniform cut-off
@@ -93,11 +99,11 @@ __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KPa
             }
         } else if (job.mode == kModePairwise) {
             tri_decode(item, job.A.n, ai, bi);
-            if (PRUNE && job.cut) cut = __ldg(job.cut + item);
+            if (CUTS && job.cut) cut = __ldg(job.cut + item);
         } else {
             ai = __ldg(job.ia + item);
             bi = __ldg(job.ib + item);
-            if (PRUNE && job.cut) cut = __ldg(job.cut + item);
+            if (CUTS && job.cut) cut = __ldg(job.cut + item);
         }
         PairIn in;
         const int64_t oa = __ldg(job.A.off + ai), ob = __ldg(job.B.off + bi);
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KPa
         bool ab = false;
         float d;
         if (in.w < abs(in.La - in.Lb)) { d = EAP_FINF; ab = true; }   // no alignment inside the window
-        else d = warp_pair<F, W, PRUNE, WIN>(in, bnd, kp, cells, ab);
+        else d = warp_pair<F, W, PM, WIN>(in, bnd, kp, cells, ab);
         ++npairs;
         nab += ab ? 1 : 0;
         if (lane == 0) {
