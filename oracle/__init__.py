@@ -85,6 +85,9 @@ def _load():
             lib.orc_eabase.restype = ctypes.c_double
             lib.orc_eabase.argtypes = [P(OrcParams), f32p, ctypes.c_int, f32p, ctypes.c_int,
                                        ctypes.c_double, i64p]
+            lib.orc_subseq.restype = ctypes.c_int
+            lib.orc_subseq.argtypes = [P(OrcParams), f32p, ctypes.c_int64, f32p, ctypes.c_int, i64p, f64p,
+                                       ctypes.c_int]
             lib.orc_nn1.restype = ctypes.c_int
             lib.orc_nn1.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int,
                                     f32p, i64p, i32p, ctypes.c_int, i32p, f64p, ctypes.c_int]
@@ -133,6 +136,19 @@ def eabase(params: OrcParams, s, t, cutoff: float):
     d = _load().orc_eabase(ctypes.byref(params), _ptr(s, ctypes.c_float), len(s),
                            _ptr(t, ctypes.c_float), len(t), float(cutoff), ctypes.byref(cells))
     return d, int(cells.value)
+
+
+def subseq(params: OrcParams, T, q, nthreads: int | None = None):
+    """Sub-sequence search (Section 4.3): (position, distance) of the window
+    of T closest to q, both z-normalised; (-1, inf) if q is longer than T."""
+    T, q = _f32(T), _f32(q)
+    pos = ctypes.c_int64(-1)
+    dist = ctypes.c_double(0.0)
+    rc = _load().orc_subseq(ctypes.byref(params), _ptr(T, ctypes.c_float), len(T), _ptr(q, ctypes.c_float),
+                            len(q), ctypes.byref(pos), ctypes.byref(dist), nthreads or os.cpu_count() or 1)
+    if rc != 0:
+        raise ValueError("orc_subseq: invalid arguments")
+    return int(pos.value), float(dist.value)
 
 
 def _packed_args(p):

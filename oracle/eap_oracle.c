@@ -25,6 +25,8 @@
  *                  the strict "<" update; threads split the queries.
  *   orc_pairwise   the full distance matrix (the exact values that prune-only
  *                  mode must reproduce, Section 3 intro).
+ *   orc_subseq     sub-sequence search (Section 4.3): every z-normalised
+ *                  window of a long series against a z-normalised query.
  *   orc_envelope / orc_lb_keogh   the textbook LB_Keogh (Section 2.1, Section
  *                  4.2): windowed min/max envelope, then the sum of the costs
  *                  to the envelope outside it.
@@ -521,6 +523,79 @@ int orc_pairwise(const orc_params* p, const float* d, const int64_t* o, const in
  * LB_Keogh (textbook form): envelope of Q with window w, then the cost of
  * each point of C that lies outside it to the nearest envelope edge.
  * ------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------
+ * Sub-sequence search (Section 4.3): the start position i of the window of
+ * the long series T that minimises D(znorm(Q), znorm(T[i .. i+m-1])).
+ * z-normalisation: subtract the mean, divide by the population standard
+ * deviation (two passes, in double); a window whose deviation is at most
+ * 1e-8 normalises to zeros.  Every position is evaluated in full with the
+ * definition of D (orc_distance on the normalised windows); ties keep the
+ * lowest position.  Threads split the positions.
+ * ------------------------------------------------------------------------ */
+static void o_znorm(const float* x, int m, double* z) {
+    double mu = 0.0;
+    for (int k = 0; k < m; k++) mu += (double)x[k];
+    mu /= (double)m;
+    double var = 0.0;
+    for (int k = 0; k < m; k++) var += ((double)x[k] - mu) * ((double)x[k] - mu);
+    var /= (double)m;
+    const double sd = sqrt(var);
+    for (int k = 0; k < m; k++) z[k] = sd > 1e-8 ? ((double)x[k] - mu) / sd : 0.0;
+}
+
+typedef struct {
+    const orc_params* p;
+    const float* T; const double* zq;
+    int m;
+    int64_t begin, end;
+    int64_t best_pos; double best;
+} o_ss_job;
+
+static void* o_ss_worker(void* arg) {
+    o_ss_job* jb = (o_ss_job*)arg;
+    double* z = (double*)malloc(sizeof(double) * (size_t)jb->m);
+    jb->best = OINF;
+    jb->best_pos = -1;
+    for (int64_t i = jb->begin; i < jb->end; i++) {
+        o_znorm(jb->T + i, jb->m, z);
+        const double d = orc_distance_d(jb->p, jb->zq, jb->m, z, jb->m);
+        if (d < jb->best) { jb->best = d; jb->best_pos = i; }
+    }
+    free(z);
+    return NULL;
+}
+
+int orc_subseq(const orc_params* p, const float* T, int64_t n, const float* q, int m,
+               int64_t* out_pos, double* out_dist, int nthreads) {
+    *out_pos = -1;
+    *out_dist = OINF;
+    if (m <= 0) return -1;
+    const int64_t npos = n - m + 1;
+    if (npos <= 0) return 0;
+    double* zq = (double*)malloc(sizeof(double) * (size_t)m);
+    o_znorm(q, m, zq);
+    if (p->derivative) {
+        /* Not defined for sub-sequence search here. */
+        free(zq);
+        return -1;
+    }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > npos) nthreads = (int)npos;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    o_ss_job* jobs = (o_ss_job*)malloc(sizeof(o_ss_job) * (size_t)nthreads);
+    for (int k = 0; k < nthreads; k++) {
+        jobs[k] = (o_ss_job){p, T, zq, m, npos * k / nthreads, npos * (k + 1) / nthreads, -1, OINF};
+        pthread_create(&th[k], NULL, o_ss_worker, &jobs[k]);
+    }
+    for (int k = 0; k < nthreads; k++) {
+        pthread_join(th[k], NULL);
+        /* Threads cover increasing positions: strict < keeps the lowest on ties. */
+        if (jobs[k].best < *out_dist) { *out_dist = jobs[k].best; *out_pos = jobs[k].best_pos; }
+    }
+    free(th); free(jobs); free(zq);
+    return 0;
+}
+
 void orc_envelope(const float* q, int L, long w, double* upper, double* lower) {
     for (int i = 0; i < L; i++) {
         double u = -OINF, lo = OINF;

@@ -485,3 +485,55 @@ def test_eabase_erp_row_minimum_includes_the_vertical_border():
     assert O.distance(p, s, t) == 0.0
     assert O.eabase(p, s, t, 4.0)[0] == 0.0
     assert O.eapruned(p, s, t, 4.0)[0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Sub-sequence search (Section 4.3): z-normalised windows of a long series.
+
+def _znorm_np(x):
+    x = np.asarray(x, dtype=np.float64)
+    mu = x.mean()
+    sd = np.sqrt(((x - mu) ** 2).mean())
+    return (x - mu) / sd if sd > 1e-8 else np.zeros_like(x)
+
+
+def test_subseq_finds_a_planted_copy_and_ignores_scale_and_offset():
+    T = _walks(1, 4000, 21)[0]
+    q = T[1717:1717 + 96].copy()
+    p = O.make_params("cdtw", window_ratio=0.1)
+    assert O.subseq(p, T, q) == (1717, 0.0)
+    pos, d = O.subseq(p, T, (q * np.float32(2.5) - np.float32(4.0)).astype(np.float32))
+    assert pos == 1717 and d < 1e-9
+
+
+def test_subseq_window_zero_is_znormalised_euclidean_search():
+    T = _walks(1, 1500, 22)[0]
+    q = _walks(1, 40, 23)[0]
+    win = np.lib.stride_tricks.sliding_window_view(T.astype(np.float64), 40)
+    zq = _znorm_np(q)
+    ed = np.array([((zq - _znorm_np(w)) ** 2).sum() for w in win])
+    pos, d = O.subseq(O.make_params("cdtw", window=0), T, q)
+    assert pos == int(np.argmin(ed))
+    assert abs(d - ed.min()) <= 1e-12 * ed.min()
+
+
+def test_subseq_equals_bruteforce_paths_on_tiny_series():
+    rng = np.random.default_rng(24)
+    for kind, kw in [("dtw", {}), ("cdtw", {"window": 1})]:
+        T = rng.uniform(-2, 2, 14).astype(np.float32)
+        q = rng.uniform(-2, 2, 4).astype(np.float32)
+        zq = list(_znorm_np(q))
+        d_bf = [brute.brute_distance(kind, zq, list(_znorm_np(T[i:i + 4])), 0, **kw) for i in range(11)]
+        pos, d = O.subseq(O.make_params(kind, **kw), T, q)
+        assert pos == int(np.argmin(d_bf))
+        assert abs(d - min(d_bf)) <= 1e-12 * max(1.0, min(d_bf))
+
+
+def test_subseq_edge_cases():
+    p = O.make_params("dtw")
+    T = _walks(1, 50, 25)[0]
+    assert O.subseq(p, T[:10], T[:11]) == (-1, math.inf)     # query longer than the series
+    assert O.subseq(p, T[:10], T[:10]) == (0, 0.0)           # one position
+    flat = np.concatenate([T[:20], np.full(12, 3.0, np.float32), T[20:]]).astype(np.float32)
+    pos, d = O.subseq(p, flat, np.full(12, -1.0, np.float32))
+    assert pos == 20 and d == 0.0                             # constant windows normalise to zeros
