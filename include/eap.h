@@ -197,6 +197,36 @@ int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_se
                       const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
                       void* cuda_stream, eap_stats* opt_stats);
 
+/* ---- sub-sequence search ---------------------------------------------------
+ * Sub-sequence search (Section 4.3): for every query Q_q, the start position
+ * i in [0, n - L_q] of the long series `ref` that minimises
+ * D(znorm(Q_q), znorm(ref[i .. i + L_q - 1])), D = DTW or CDTW (p->kind;
+ * window w = floor(window_ratio * L_q) or p->window), computed with
+ * EAPruned (p->prune must be 1; p->derivative 0; p->lb is ignored: both
+ * LB_Keogh directions are always used).  znorm subtracts the window's mean
+ * and divides by its population standard deviation; a deviation of at most
+ * 1e-8 normalises the window to zeros.  Ties keep the lowest position.
+ * Per query, on the stream: sliding means and deviations of every window;
+ * for every window the squared Euclidean distance of the normalised window
+ * (its diagonal path: an upper bound of D) and LB_Keogh both ways (query
+ * envelope vs window, the series' running envelope normalised like the
+ * window vs query); the smallest upper bound seeds the cut-off; the windows
+ * whose bound does not exceed it are compacted in position order, normalised
+ * into scratch in chunks of at most 256 MB and searched by the 1-NN DP with
+ * the shared best-so-far (the bound skips a window once the best-so-far
+ * falls below it, Alg. 2).
+ *   ref       device float[n], 0 <= n < 2^31
+ *   queries   series set (device + host mirrors), lengths 1..8192
+ *   out_pos   device int64[queries->count]: start position, -1 when L_q > n
+ *   out_dist  device float[queries->count]: D, +inf when L_q > n
+ * Scratch: about 44 bytes per point of ref plus the chunk buffer, stream-
+ * ordered.  The call synchronises the stream once per query (to size the
+ * chunks).  opt_stats: pairs = windows, pairs_lb_pruned = windows the bounds
+ * removed, cells as in eap_nn1 (effective = windows x L_q^2).
+ * Errors: EAP_EINVAL for other distances or modes, EAP_ENOMEM, EAP_EDEVICE. */
+int eap_subseq(const eap_params* p, const float* ref, int64_t n, const eap_series_set* queries,
+               int64_t* out_pos, float* out_dist, void* cuda_stream, eap_stats* opt_stats);
+
 /* ---- batched uneven workloads ---------------------------------------------
  * Many independent 1-NN problems (datasets of different lengths, sizes and
  * distances) in one persistent DP launch: every (task, query, candidate)

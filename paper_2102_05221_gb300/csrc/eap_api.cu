@@ -1129,6 +1129,9 @@ void map_set(int kind, int cost, int bucket, int m) {
     g_map[kind][cost][bucket] = m;
 }
 int pick_w(int kind, int cost, int max_cols, int prune) { return choose_w(kind, cost, max_cols, prune); }
+int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
+    return choose_cta(kind, cost, max_rows, max_cols, prune);
+}
 int bucket_of(int len) { return length_bucket(len); }
 int resolve_cost_ext(const eap_params* p) { return resolve_cost(p); }
 int validate_set_ext(const eap_series_set* s, int* max_len) { return validate_set(s, max_len); }

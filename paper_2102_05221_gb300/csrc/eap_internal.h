@@ -45,6 +45,7 @@ void tune_set(int kind, int cost, int bucket, int w);
 void tune_reset();
 void map_set(int kind, int cost, int bucket, int m);   // 0 untuned, 1 warp, 2 CTA
 int pick_w(int kind, int cost, int max_cols, int prune);
+int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).

@@ -96,7 +96,8 @@ def load(build_if_missing: bool = True):
             lib.eap_serve_poll.argtypes = [vp, u64, P(i32), P(ctypes.c_float)]
             lib.eap_serve_drain.argtypes = [vp, i32]
             lib.eap_serve_destroy.argtypes = [vp]
-        for name in ("eap_nn1", "eap_nn1_host", "eap_pairwise", "eap_pairs", "eap_lb_keogh"):
+        lib.eap_subseq.argtypes = [P(eap_params), vp, ctypes.c_int64, P(eap_series_set), vp, vp, vp, P(eap_stats)]
+        for name in ("eap_nn1", "eap_nn1_host", "eap_pairwise", "eap_pairs", "eap_lb_keogh", "eap_subseq"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -277,6 +278,28 @@ def eap_lb_keogh(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, stream=None)
                           ctypes.c_void_p(ib.data_ptr()), ctypes.c_void_p(out.data_ptr()), n, _stream_ptr(stream))
     _check(rc, "eap_lb_keogh")
     return out
+
+
+def eap_subseq(p: eap_params, ref, queries: SeriesSet, stream=None, with_stats: bool = False):
+    """Sub-sequence search (Section 4.3): for every query, the start position
+    of the window of the long series `ref` (a 1-D float32 array or device
+    tensor) closest to it under z-normalised DTW / CDTW.  Returns device
+    tensors (pos int64, dist float32) [and the stats]."""
+    torch = _torch()
+    lib = load()
+    dev = queries.data.device
+    r = ref if isinstance(ref, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(ref, dtype=np.float32))
+    r = r.to(device=dev, dtype=torch.float32).contiguous()
+    pos = torch.empty(queries.count, dtype=torch.int64, device=dev)
+    dist = torch.empty(queries.count, dtype=torch.float32, device=dev)
+    sq = queries.struct()
+    st = eap_stats()
+    rc = lib.eap_subseq(ctypes.byref(p), ctypes.c_void_p(r.data_ptr() if r.numel() else None), int(r.numel()),
+                        ctypes.byref(sq), ctypes.c_void_p(pos.data_ptr() if pos.numel() else None),
+                        ctypes.c_void_p(dist.data_ptr() if dist.numel() else None), _stream_ptr(stream),
+                        ctypes.byref(st) if with_stats else None)
+    _check(rc, "eap_subseq")
+    return (pos, dist, st.as_dict()) if with_stats else (pos, dist)
 
 
 def eap_pairs_noalloc(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, cutoff=None, stream=None,

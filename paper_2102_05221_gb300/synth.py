@@ -143,6 +143,40 @@ def uniform_values(n: int, lengths, seed: int, lo: float = -3.0, hi: float = 3.0
 # The five workload shapes (configuration recipes; sizes are the workloads').
 # --------------------------------------------------------------------------
 
+def long_series(n: int, seed: int, seg=(200, 2000), n_classes: int = 10) -> np.ndarray:
+    """A long series standing in for the references of sub-sequence search
+    (Section 4.3): back-to-back segments of log-uniform length in `seg`, each
+    a z-normalised random walk plus a class sine template (values O(1))."""
+    rng = _rng(seed)
+    lo, hi = seg
+    out, total = [], 0
+    while total < n:
+        L = int(np.clip(np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi)))), lo, hi))
+        y = rng.integers(0, n_classes, size=1)
+        out.append(labelled_series(rng, y, L)[0])
+        total += L
+    return np.concatenate(out)[:n].astype(np.float32)
+
+
+def subseq_queries(T: np.ndarray, lengths, seed: int, planted: bool = True, noise: float = 0.1):
+    """Queries for sub-sequence search: a window of T at a random position
+    plus N(0, noise) (planted), or an independent labelled series.  Returns
+    (Packed, positions) with position -1 for queries that were not planted."""
+    rng = _rng(seed)
+    out, where = [], []
+    for m in lengths:
+        m = int(m)
+        if planted and m <= len(T):
+            p = int(rng.integers(0, len(T) - m + 1))
+            out.append((T[p:p + m] + rng.normal(0.0, noise, m)).astype(np.float32))
+            where.append(p)
+        else:
+            y = rng.integers(0, 10, size=1)
+            out.append(labelled_series(rng, y, m)[0])
+            where.append(-1)
+    return pack(out), np.asarray(where, dtype=np.int64)
+
+
 def seed_for(config: int, dataset: int = 0) -> int:
     return BASE_SEED + config * 1000 + dataset
 
