@@ -222,7 +222,8 @@ def main():
     ap.add_argument("--mode", default="per-distance", choices=["per-distance", "batch"],
                     help="per-distance: one eap_nn1 call per distance; batch: all six in one eap_nn1_batch launch")
     ap.add_argument("--workload", default="nn1_512",
-                    choices=["nn1_512", "unpruned_512", "modes_512", "allpairs_4096", "uneven_64", "serving"],
+                    choices=["nn1_512", "unpruned_512", "modes_512", "subseq", "allpairs_4096", "uneven_64",
+                             "serving"],
                     help="nn1_512 is the benchmark; the others measure the remaining workloads")
     args = ap.parse_args()
     kinds = [k for k in args.kinds.split(",") if k]
@@ -520,6 +521,57 @@ def workload_modes_512(args):
             "per_distance": out}
 
 
+def workload_subseq(args):
+    """Sub-sequence search (Section 4.3): a 16M-point series, queries of 128 to
+    1024 points planted with N(0, 0.1) noise, CDTW (10% window) and DTW."""
+    import time
+
+    import torch
+
+    import oracle as O
+    from paper_2102_05221_gb300 import eap, synth
+    n = 1 << 24
+    T = synth.long_series(n, synth.seed_for(6))
+    lens = [128, 128, 256, 256, 512, 512, 1024, 1024]
+    Qp, planted = synth.subseq_queries(T, lens, synth.seed_for(6, 1), planted=True, noise=0.1)
+    Tdev = torch.from_numpy(T).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for kind, kw in (("cdtw", {"window_ratio": 0.1}), ("dtw", {})):
+        p = eap.params(kind, **kw)
+        per_len = {}
+        for m in sorted(set(lens)):
+            sel = [k for k, L in enumerate(lens) if L == m]
+            Q = eap.SeriesSet.from_packed(synth.pack([Qp.series(k) for k in sel]))
+            for _ in range(max(1, args.warmup)):
+                eap.eap_subseq(p, Tdev, Q)
+            ms = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                ms.append(_sync_time(lambda: eap.eap_subseq(p, Tdev, Q)))
+            pos, dist, st = eap.eap_subseq(p, Tdev, Q, with_stats=True)
+            t = sorted(ms)[len(ms) // 2] / len(sel)
+            per_len[m] = {"ms_per_query": t, "windows_per_s": (n - m + 1) / (t / 1e3),
+                          "windows_pruned_by_bounds": st["pairs_lb_pruned"] / st["pairs"],
+                          "cells_computed_over_effective": st["cells_computed"] / max(1, st["cells_effective"]),
+                          "found_planted": int(sum(int(a) == int(planted[k]) for a, k in zip(pos.cpu().numpy(), sel)))}
+        out[kind] = per_len
+    # The oracle (every window in full, FP64) on a bounded sample of windows of one 256-point query.
+    q = Qp.series(2)
+    sample = 4000
+    t0 = time.perf_counter()
+    O.subseq(O.make_params("cdtw", window_ratio=0.1), T[:sample + 255], q)
+    cpu_wps = sample / (time.perf_counter() - t0)
+    head = out["cdtw"][256]["windows_per_s"]
+    return {"metric": "sub-sequence search windows/s (16M-point series, z-normalised CDTW 10%, 256-point queries)",
+            "value": head, "unit": "windows/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "subseq_16M", "n": n, "query_lengths": lens, "noise": 0.1,
+                       "l2": "flushed before each call (512 MiB write); series 64 MB < L2 not guaranteed resident"},
+            "per_distance": out,
+            "cpu_baseline": {"value": cpu_wps, "unit": "windows/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{sample} windows of one 256-point query, CDTW 10%, every window in full"}}
+
+
 def workload_allpairs_4096(args):
     """256 random walks of length 4096: full DTW and MSM matrices, prune-only."""
     import torch
@@ -696,7 +748,7 @@ def run_other_workload(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     from paper_2102_05221_gb300 import eap
     eap.load()
-    fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512,
+    fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512, "subseq": workload_subseq,
           "allpairs_4096": workload_allpairs_4096,
           "uneven_64": workload_uneven_64, "serving": workload_serving}[args.workload]
     line = fn(args)
