@@ -180,11 +180,12 @@ int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_
  * library and that every device loading libeap holds until the process
  * exits.  Nothing is allocated by the call: no cudaMalloc, cudaMallocAsync
  * or cudaFree.
- *   - Limit: the scratch must fit in 4 MiB.  Only ERP and the derivative
- *     variants use more than a few KB: each needs 4 bytes per element of
- *     both sets (a->data_len + b->data_len <= about 1,000,000 floats, half
- *     that for a derivative ERP); WDTW needs 128 KB.  Larger requests return
- *     EAP_EINVAL without launching anything.
+ *   - Limit: the scratch must fit in 4 MiB.  ERP and the derivative
+ *     variants each need 4 bytes per element of both sets; ERP, MSM and TWE
+ *     also need 16 bytes per element of set a (+16) for their precomputed
+ *     row constants; WDTW needs 128 KB.  (MSM: a->data_len up to about
+ *     260,000; ERP: about 24 bytes per element of a plus 4 per element of b.)
+ *     Larger requests return EAP_EINVAL without launching anything.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
  *     stream capture.

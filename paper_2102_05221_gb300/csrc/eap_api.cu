@@ -508,7 +508,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
 
     Scratch sc;
     auto layout = [&]() {
-        struct { unsigned long long *best, *ctr, *stats; float* ub; int32_t* order; float *bq, *br, *wt, *lb, *qU, *qL, *rU, *rL; } L;
+        struct { unsigned long long *best, *ctr, *stats; float* ub; int32_t* order; float *bq, *br, *wt, *lb, *qU, *qL, *rU, *rL; float4* rp; } L;
         L.best = (unsigned long long*)sc.take(sizeof(unsigned long long) * nq);
         L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
         L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
@@ -522,6 +522,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
         L.qL = use_lb ? (float*)sc.take(sizeof(float) * (size_t)qs->data_len) : nullptr;
         L.rU = use_lb2 ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
         L.rL = use_lb2 ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
+        L.rp = eaph::kind_packed(p->kind) ? (float4*)sc.take(sizeof(float4) * ((size_t)qs->data_len + 1)) : nullptr;
         return L;
     };
     layout();
@@ -562,6 +563,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.job.bnd_stride = ((mq + 1) + 31) & ~31;
     c.kp = make_kparams(p);
     c.kp.wdtw_w = d_wt;
+    c.rowpack = L.rp;
     c.kind = p->kind;
     c.cost = cost;
     // Prune (3) runs the EAPruned kernel with each pair's own diagonal bound as cut-off.
@@ -781,12 +783,13 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
 
     Scratch sc;
     auto layout = [&]() {
-        struct { unsigned long long *ctr, *stats; float *ub, *bs, *wt; } L;
+        struct { unsigned long long *ctr, *stats; float *ub, *bs, *wt; float4* rp; } L;
         L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
         L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
         L.ub = prune ? (float*)sc.take(sizeof(float) * (items ? items : 1)) : nullptr;
         L.bs = erp ? (float*)sc.take(sizeof(float) * (size_t)set->data_len) : nullptr;
         L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        L.rp = eaph::kind_packed(p->kind) ? (float4*)sc.take(sizeof(float4) * ((size_t)set->data_len + 1)) : nullptr;
         return L;
     };
     layout();
@@ -816,6 +819,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.job.bnd_stride = ((mx + 1) + 31) & ~31;
         c.kp = make_kparams(p);
         c.kp.wdtw_w = L.wt;
+        c.rowpack = L.rp;
         c.kind = p->kind;
         c.cost = cost;
         c.prune = prune ? 1 : 0;
@@ -870,12 +874,13 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     const int cost = resolve_cost(p);
     Scratch sc;
     auto layout = [&]() {
-        struct { unsigned long long *ctr, *stats; float *ba, *bb, *wt; } L;
+        struct { unsigned long long *ctr, *stats; float *ba, *bb, *wt; float4* rp; } L;
         L.ctr = (unsigned long long*)sc.take(sizeof(unsigned long long));
         L.stats = (unsigned long long*)sc.take(sizeof(unsigned long long) * kStatCount);
         L.ba = erp ? (float*)sc.take(sizeof(float) * (size_t)a->data_len) : nullptr;
         L.bb = erp ? (float*)sc.take(sizeof(float) * (size_t)b->data_len) : nullptr;
         L.wt = wdtw ? (float*)sc.take(sizeof(float) * (2 * kWdtwOff + 1)) : nullptr;
+        L.rp = eaph::kind_packed(p->kind) ? (float4*)sc.take(sizeof(float4) * ((size_t)a->data_len + 1)) : nullptr;
         return L;
     };
     layout();
@@ -907,6 +912,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.job.bnd_stride = ((ma + 1) + 31) & ~31;
     c.kp = make_kparams(p);
     c.kp.wdtw_w = L.wt;
+    c.rowpack = L.rp;
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune;
@@ -1027,6 +1033,8 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     const bool deriv = p->derivative != 0;
     const size_t o_da = deriv ? take(sizeof(float) * (size_t)a->data_len) : 0;
     const size_t o_db = deriv ? take(sizeof(float) * (size_t)b->data_len) : 0;
+    const bool packed = eaph::kind_packed(p->kind);
+    const size_t o_rp = packed ? take(sizeof(float4) * ((size_t)a->data_len + 1)) : 0;
     if (used > kNoAllocScratchBytes) return EAP_EINVAL;
     void* base = nullptr;
     if ((rc = noalloc_scratch(&base))) return rc;
@@ -1075,6 +1083,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.job.bnd_stride = ((ma + 1) + 31) & ~31;
     c.kp = make_kparams(p);
     c.kp.wdtw_w = d_wt;
+    c.rowpack = packed ? (float4*)(s + o_rp) : nullptr;
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune;
@@ -1145,6 +1154,25 @@ void launch_erp_border(const eap_series_set* s, float gap, int cost, float* bord
 }
 void launch_derivative(const eap_series_set* s, float* out, cudaStream_t st) {
     launch_derivative_set(s, out, device_sms(), st);
+}
+bool kind_packed(int kind) { return kind == EAP_ERP || kind == EAP_MSM || kind == EAP_TWE; }
+int launch_rowpack(int kind, int cost, const eap_series_set* s, const KParams& kp, float4* out, cudaStream_t st) {
+    if (s->count <= 0) return 0;
+    const SeriesDev S{s->data, s->offsets, s->lengths, nullptr, s->count};
+    const int blocks = std::min(s->count, std::max(1, device_sms()) * 8);
+    switch (kind) {
+        case EAP_ERP:
+            if (cost) rowpack_kernel<FErp<1>><<<blocks, 128, 0, st>>>(S, kp, out);
+            else rowpack_kernel<FErp<0>><<<blocks, 128, 0, st>>>(S, kp, out);
+            break;
+        case EAP_MSM: rowpack_kernel<FMsm><<<blocks, 128, 0, st>>>(S, kp, out); break;
+        case EAP_TWE:
+            if (cost) rowpack_kernel<FTwe<1>><<<blocks, 128, 0, st>>>(S, kp, out);
+            else rowpack_kernel<FTwe<0>><<<blocks, 128, 0, st>>>(S, kp, out);
+            break;
+        default: return 0;
+    }
+    return (int)cudaGetLastError();
 }
 void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st) {
     wdtw_table_kernel<<<(2 * kWdtwOff + 256) / 256, 256, 0, st>>>(tab, (double)g, (double)wmax);

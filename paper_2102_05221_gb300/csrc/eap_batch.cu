@@ -49,6 +49,7 @@ struct TaskDev {
     int32_t* order;              // [nq x nr]
     float* ub;                   // [nq x nr]
     const float* lb;             // [nq x nr] or null
+    const float4* rp;            // packed row constants of the queries (ERP, MSM, TWE) or null
     int32_t* out_idx;
     float* out_dist;
     unsigned long long begin;    // first work item of the task
@@ -95,6 +96,7 @@ __device__ void fill_pair(const TaskDev& T, int q, int c, PairIn& in) {
     in.bB = T.B.border ? T.B.border + ob : nullptr;
     in.wt = T.wt ? T.wt + kWdtwOff - max(in.La, in.Lb) : nullptr;
     in.cut_src = T.best + q;
+    in.rp = T.rp ? T.rp + oa : nullptr;
     in.w = pair_window(T.kp, in.La, in.Lb);
     in.cut = EAP_FINF;
 }
@@ -260,7 +262,7 @@ struct HostTask {
     int src;            // index in the caller's array
     int fn, W, cost;
     int nq, nr, mq, mr;
-    bool erp, wdtw, lb, lb2, deriv;
+    bool erp, wdtw, lb, lb2, deriv, packed;
 };
 
 int device_sms_b() {
@@ -301,6 +303,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         h.lb = tk.params.lb != EAP_LB_NONE && (tk.params.kind == EAP_DTW || tk.params.kind == EAP_CDTW);
         h.lb2 = h.lb && tk.params.lb == EAP_LB_KEOGH2;
         h.deriv = tk.params.derivative != 0;
+        h.packed = eaph::kind_packed(tk.params.kind);
         ht.push_back(h);
         max_rows = std::max(max_rows, mq);
     }
@@ -321,7 +324,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
     const size_t o_tasks = take(sizeof(TaskDev) * nt);
     const size_t o_ctr = take(sizeof(unsigned long long));
     const size_t o_stats = take(sizeof(unsigned long long) * kStatCount);
-    struct Off { size_t best, ub, order, lb, qU, qL, rU, rL, bq, br, wt, dq, dr; };
+    struct Off { size_t best, ub, order, lb, qU, qL, rU, rL, bq, br, wt, dq, dr, rp; };
     std::vector<Off> off(nt);
     for (int k = 0; k < nt; ++k) {
         const HostTask& h = ht[k];
@@ -350,6 +353,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
             o.dq = take(sizeof(float) * (size_t)tk.queries.data_len);
             o.dr = take(sizeof(float) * std::max<int64_t>(tk.refs.data_len, 1));
         }
+        if (h.packed) o.rp = take(sizeof(float4) * ((size_t)tk.queries.data_len + 1));
     }
     // The sets each task's kernels read: the caller's, or (derivative variants,
     // Section 2.3) copies whose data are the first-derivative series.
@@ -387,6 +391,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         t.ub = (float*)(base + o.ub);
         t.order = (int32_t*)(base + o.order);
         t.lb = (h.lb && h.nr > 0) ? (const float*)(base + o.lb) : nullptr;
+        t.rp = h.packed ? (const float4*)(base + o.rp) : nullptr;
         t.out_idx = tk.out_idx;
         t.out_dist = tk.out_dist;
         t.begin = items;
@@ -422,6 +427,9 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
             eaph::launch_erp_border(&rset[k], tk.params.erp_gap, h.cost, (float*)(base + o.br), st);
         }
         if (h.wdtw) eaph::launch_wdtw_table((float*)(base + o.wt), tk.params.wdtw_g, tk.params.wdtw_wmax, st);
+        if (h.packed)
+            e |= eaph::launch_rowpack(tk.params.kind, h.cost, &qset[k], eaph::kparams_of(&tk.params),
+                                      (float4*)(base + o.rp), st);
         if (h.lb && h.nr > 0)
             eaph::launch_lb(&tk.params, &qset[k], &rset[k], h.lb2 ? 1 : 0, (float*)(base + o.qU), (float*)(base + o.qL),
                             h.lb2 ? (float*)(base + o.rU) : nullptr, h.lb2 ? (float*)(base + o.rL) : nullptr,

@@ -112,6 +112,7 @@ struct FDtw {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
+    static constexpr bool kPacked = false;   // the row constant is s_i itself
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -133,6 +134,7 @@ struct FWdtw {
     static constexpr bool kWeights = true;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
+    static constexpr bool kPacked = false;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -154,8 +156,11 @@ struct FErp {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = true;
+    static constexpr bool kPacked = true;    // row constants precomputed per point (rowpack_kernel)
     struct Col { float t, ct; };
     struct Row { float s, cs; };
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.cs, 0.f, 0.f); }
+    __device__ static Row unpack(const float4& p) { return {p.x, p.y}; }
     __device__ static Col col(float t, float, const KParams& kp) { return {t, pcost<COST>(t, kp.erp_gap)}; }
     __device__ static Row row(float s, float, const KParams& kp, const float*) {
         return {s, pcost<COST>(s, kp.erp_gap)};
@@ -182,8 +187,11 @@ struct FMsm {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kBorders = false;
+    static constexpr bool kPacked = true;
     struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
     struct Row { float s, sge, ec; };   // e = s_{i-1} - s_i: sge = sign(e), ec = c + |e|
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sge, r.ec, 0.f); }
+    __device__ static Row unpack(const float4& p) { return {p.x, p.y, p.z}; }
     __device__ static Col col(float t, float tprev, const KParams& kp) {
         const float g = __fsub_rn(tprev, t);
         return {t, g >= 0.f ? -1.f : 1.f, __fadd_rn(kp.msm_c, fabsf(g))};
@@ -210,8 +218,11 @@ struct FTwe {
     // diagonal predecessor: the strip carries it from the previous row.
     static constexpr bool kCarry = true;
     static constexpr bool kBorders = false;
+    static constexpr bool kPacked = true;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
     struct Row { float s, sprev, ga; };   // ga = cost(s_i, s_{i-1}) + nu + lambda
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sprev, r.ga, 0.f); }
+    __device__ static Row unpack(const float4& p) { return {p.x, p.y, p.z}; }
     __device__ static Col col(float t, float tprev, const KParams& kp) {
         return {t, tprev, __fadd_rn(__fadd_rn(pcost<COST>(t, tprev), kp.twe_nu), kp.twe_lambda)};
     }
@@ -246,6 +257,7 @@ struct PairIn {
     const float* bA;     // ERP: bA[k] = M(k+1, 0) unwindowed prefix sum over A (else unused)
     const float* bB;     // ERP: bB[k] = M(0, k+1)
     const float* wt;     // WDTW: weight of |i-j| = d is wt[2d]
+    const float4* rp;    // packed row constants of A (rp[i-1] for row i; one readable entry past La) when F::kPacked
     const unsigned long long* cut_src;  // best-so-far to refresh from (nn1), or null
     int La, Lb;
     int w;               // window (kNoWindow when none)
@@ -418,8 +430,16 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         const bool lane_out = c0 > Lb;             // strip entirely past the last column
         const int nvalid = max(0, min(W, Lb - c0 + 1));
         const bool st31 = !last && lane == 31;     // this lane hands its last column to the next panel
-        float sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
-        float s_next = __ldg(in.A + r0 - 1);
+        // Row constants: computed from s_i, s_{i-1} per step, or (F::kPacked)
+        // loaded precomputed, one step ahead.
+        float sp = 0.f, s_next = 0.f;
+        float4 pk_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (F::kPacked) {
+            pk_next = __ldg(in.rp + r0 - 1);
+        } else {
+            sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
+            s_next = __ldg(in.A + r0 - 1);
+        }
         const int nsteps = r1 - r0 + 32;
         bool ea_handed = false;   // EABase: lane 31 handed a value <= eacut to the next panel
 
@@ -433,12 +453,18 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1);
             if (lane == 0) x = bv;
             if (act) {
-                const float s = s_next;
-                s_next = __ldg(in.A + min(row, La - 1));
-                const typename F::Row rc = F::row(s, sp, kp, in.wt);
+                typename F::Row rc;
+                if constexpr (F::kPacked) {
+                    rc = F::unpack(pk_next);
+                    pk_next = __ldg(in.rp + row);   // row <= La: the entry past La is readable
+                } else {
+                    const float s = s_next;
+                    s_next = __ldg(in.A + min(row, La - 1));
+                    rc = F::row(s, sp, kp, in.wt);
+                    sp = s;
+                }
                 shift_weights<F, W>(wr, in.wt, row, c0);
                 strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
-                sp = s;
                 dg = x;
                 if (st31) {
                     bnd[row] = v[W - 1];

@@ -18,6 +18,7 @@ struct LaunchCtx {
     int cost;            // resolved: 0 squared, 1 absolute
     int W;               // strip width per lane (4, 8 or 16)
     int prune;           // 1 EAPruned, 0 Base, 2 EABase (eapd::kPm*)
+    float4* rowpack;     // scratch of A.data_len + 1 float4 for the packed row constants (ERP, MSM, TWE)
     int sms;             // multiprocessors of the device
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
@@ -53,6 +54,11 @@ void launch_erp_border(const ::eap_series_set* s, float gap, int cost, float* bo
 void launch_wdtw_table(float* tab, float g, float wmax, cudaStream_t st);
 // First-derivative series of every series of s into out (same layout as s->data).
 void launch_derivative(const ::eap_series_set* s, float* out, cudaStream_t st);
+// Whether a distance's DP takes packed row constants (LaunchCtx::rowpack), and
+// their computation for one set (kind/cost resolved; out: data_len + 1 float4).
+bool kind_packed(int kind);
+int launch_rowpack(int kind, int cost, const ::eap_series_set* s, const eapd::KParams& kp, float4* out,
+                   cudaStream_t st);
 void launch_lb(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int two_way,
                float* qU, float* qL, float* rU, float* rL, float* lb, cudaStream_t st);
 eapd::KParams kparams_of(const ::eap_params* p);
@@ -138,16 +144,33 @@ int run_cta(const LaunchCtx& c) {
     return (int)cudaGetLastError();
 }
 
+// Packed row constants of the row set (F::kPacked) into c.rowpack.
+template <class F>
+int run_rowpack(const LaunchCtx& c) {
+    using namespace eapd;
+    if (!c.rowpack) return (int)cudaErrorInvalidValue;
+    if (c.job.A.n <= 0) return 0;
+    const int blocks = std::min(c.job.A.n, std::max(1, c.sms) * 8);
+    rowpack_kernel<F><<<blocks, 128, 0, c.stream>>>(c.job.A, c.kp, c.rowpack);
+    return (int)cudaGetLastError();
+}
+
 template <class F, bool WIN>
 int run_kind(const LaunchCtx& c, bool ub_only) {
     if (ub_only) return run_ub<F>(c);
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(c) : run_cta<F, 4>(c);
     }
+    LaunchCtx d = c;
+    if constexpr (F::kPacked) {
+        const int e = run_rowpack<F>(c);
+        if (e) return e;
+        d.job.rowpack = c.rowpack;
+    }
     switch (c.W) {
-        case 4: return run_dp<F, 4, WIN>(c);
-        case 8: return run_dp<F, 8, WIN>(c);
-        case 16: return run_dp<F, 16, WIN>(c);
+        case 4: return run_dp<F, 4, WIN>(d);
+        case 8: return run_dp<F, 8, WIN>(d);
+        case 16: return run_dp<F, 16, WIN>(d);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -41,6 +41,7 @@ struct DPJob {
     unsigned long long* stats;         // kStatCount counters
     const float* wdtw_table;           // universal WDTW weight table (or null)
     const float* lb;                   // optional per-item lower bound (nn1: [A.n x B.n] by candidate), or null
+    const float4* rowpack;             // packed row constants of A (F::kPacked), laid out like A.data, or null
     int bnd_stride;                    // floats of shared memory per warp
     int pad_;
 };
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KPa
         in.bB = job.B.border ? job.B.border + ob : nullptr;
         in.wt = job.wdtw_table ? job.wdtw_table + kWdtwOff - max(in.La, in.Lb) : nullptr;
         in.cut_src = cut_src;
+        in.rp = job.rowpack ? job.rowpack + oa : nullptr;
         in.w = pair_window(kp, in.La, in.Lb);
         in.cut = cut;
         bool ab = false;
@@ -144,6 +146,22 @@ __global__ void __launch_bounds__(kThreads) dp_kernel(const DPJob job, const KPa
             if (nab) atomicAdd(job.stats + kStatAbandoned, nab);
             if (cells) atomicAdd(job.stats + kStatCells, cells);
             if (nlb) atomicAdd(job.stats + kStatLbPruned, nlb);
+        }
+    }
+}
+
+// Row constants of every point of a set, precomputed once for the DP
+// (F::kPacked): out[off + i] = F::row(x_i, x_{i-1}) with x_{-1} = 0, the
+// same function the wavefront would evaluate per step.  One block per series.
+template <class F>
+__global__ void rowpack_kernel(const SeriesDev S, const KParams kp, float4* __restrict__ out) {
+    for (int k = blockIdx.x; k < S.n; k += gridDim.x) {
+        const float* x = S.data + S.off[k];
+        float4* o = out + S.off[k];
+        const int L = S.len[k];
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const float sp = i > 0 ? __ldg(x + i - 1) : 0.f;
+            o[i] = F::pack(F::row(__ldg(x + i), sp, kp, nullptr));
         }
     }
 }
