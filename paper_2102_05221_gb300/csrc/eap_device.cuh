@@ -111,6 +111,7 @@ template <int COST>
 struct FDtw {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
+    static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;   // the row constant is s_i itself
     struct Col { float t; };
@@ -133,6 +134,7 @@ struct FWdtw {
     // row (cell_w); the table lookup in cell() serves the diagonal bound.
     static constexpr bool kWeights = true;
     static constexpr bool kCarry = false;
+    static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;
     struct Col { float t; };
@@ -155,6 +157,7 @@ template <int COST>
 struct FErp {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
+    static constexpr bool kPen = false;
     static constexpr bool kBorders = true;
     static constexpr bool kPacked = true;    // row constants precomputed per point (rowpack_kernel)
     struct Col { float t, ct; };
@@ -186,6 +189,7 @@ struct FErp {
 struct FMsm {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
+    static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
     struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
@@ -217,6 +221,10 @@ struct FTwe {
     // cost(s_{i-1}, t_{j-1}) of the match cost is cost(s_i, t_j) of the cell's
     // diagonal predecessor: the strip carries it from the previous row.
     static constexpr bool kCarry = true;
+    // The stiffness penalty nu * (|i-j| + |(i-1)-(j-1)|) = 2 nu |i-j| is
+    // constant along a diagonal: the wavefront keeps it per cell in registers
+    // and shifts it by one cell per row, like WDTW's weights.
+    static constexpr bool kPen = true;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
@@ -229,19 +237,22 @@ struct FTwe {
     __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
         return {s, sprev, __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda)};
     }
-    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float fdij,
+    // 2 nu |i - j| for a cell with i - j = d.
+    __device__ static float pen(const KParams& kp, int d) { return __fmul_rn(kp.twe_nu2, (float)abs(d)); }
+    __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int dij, float,
                                  const KParams& kp) {
         const float gm0 = __fadd_rn(pcost<COST>(r.s, c.t), pcost<COST>(r.sprev, c.tprev));
-        const float gm = __fmaf_rn(kp.twe_nu2, fabsf(fdij), gm0);
+        const float gm = __fadd_rn(gm0, pen(kp, dij));
         return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
     }
-    // The same cell with cost(s_{i-1}, t_{j-1}) given (carry_in) and
-    // cost(s_i, t_j) returned for the next row (carry_out).
-    __device__ static float cell_c(float dg, float tp, float lf, const Row& r, const Col& c, float fdij,
-                                   const KParams& kp, float carry_in, float& carry_out) {
+    // The same cell with cost(s_{i-1}, t_{j-1}) given (carry_in), the
+    // penalty given (pn = pen(i - j)) and cost(s_i, t_j) returned for the
+    // next row (carry_out).
+    __device__ static float cell_c(float dg, float tp, float lf, const Row& r, const Col& c, float pn,
+                                   float carry_in, float& carry_out) {
         const float c1 = pcost<COST>(r.s, c.t);
         carry_out = c1;
-        const float gm = __fmaf_rn(kp.twe_nu2, fabsf(fdij), __fadd_rn(c1, carry_in));
+        const float gm = __fadd_rn(__fadd_rn(c1, carry_in), pn);
         return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
     }
     __device__ static float carry_first(const Row& r, const Col& c0) { return pcost<COST>(r.sprev, c0.tprev); }
@@ -288,7 +299,7 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const f
         if constexpr (F::kCarry) {
             const float cin = carry_prev;
             carry_prev = cy[u];
-            nv = F::cell_c(dg, top, lf, rc, cc[u], __fsub_rn(fdr, (float)u), kp, cin, cy[u]);
+            nv = F::cell_c(dg, top, lf, rc, cc[u], wr[u], cin, cy[u]);
         } else if constexpr (F::kWeights) {
             nv = F::cell_w(dg, top, lf, rc, cc[u], wr[u]);
         } else {
@@ -303,21 +314,24 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const f
     }
 }
 
-// Weights of a strip for the next row: wr[u] <- wr[u-1], wr[0] <- w(|row - c0|).
+// Per-cell diagonal factors of a strip (WDTW weights, TWE penalties) for the
+// next row: wr[u] <- wr[u-1], wr[0] <- the factor of i - j = row - c0.
 template <class F, int W>
-__device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, int row, int c0) {
-    if constexpr (F::kWeights) {
+__device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, const KParams& kp, int row, int c0) {
+    if constexpr (F::kWeights || F::kPen) {
 #pragma unroll
         for (int u = W - 1; u > 0; --u) wr[u] = wr[u - 1];
-        wr[0] = __ldg(wt + 2 * abs(row - c0));
+        if constexpr (F::kWeights) wr[0] = __ldg(wt + 2 * abs(row - c0));
+        else wr[0] = F::pen(kp, row - c0);
     }
 }
-// Weights before a strip's first row r0: wr[u] = w(|r0 - 1 - (c0 + u)|).
+// Factors before a strip's first row r0: those of i - j = r0 - 1 - (c0 + u).
 template <class F, int W>
-__device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, int r0, int c0) {
+__device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, const KParams& kp, int r0, int c0) {
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         if constexpr (F::kWeights) wr[u] = __ldg(wt + 2 * abs(r0 - 1 - c0 - u));
+        else if constexpr (F::kPen) wr[u] = F::pen(kp, r0 - 1 - c0 - u);
         else wr[u] = 0.f;
     }
 }
@@ -414,7 +428,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
         float wr[W];   // weights of the strip's cells for the current row (WDTW)
-        init_weights<F, W>(wr, in.wt, r0, c0);
+        init_weights<F, W>(wr, in.wt, kp, r0, c0);
         float cy[W];   // carried per-cell values of the previous row (TWE)
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
@@ -463,7 +477,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                     rc = F::row(s, sp, kp, in.wt);
                     sp = s;
                 }
-                shift_weights<F, W>(wr, in.wt, row, c0);
+                shift_weights<F, W>(wr, in.wt, kp, row, c0);
                 strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                 dg = x;
                 if (st31) {
