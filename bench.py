@@ -44,7 +44,7 @@ KIND_PARAMS = {
 }
 # Algorithmic FP32 instructions per cell update of each distance's recurrence
 # (the minimum the cell needs: see the functors in csrc/eap_device.cuh).
-OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 11, "twe": 7}
+OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 9, "twe": 7}
 # Kernels this library launches per eap_nn1 call: init, upper bound, sort,
 # DP, unpack; ERP adds two border kernels, WDTW one weight table.
 LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 7, "msm": 5, "twe": 5}

@@ -178,38 +178,46 @@ struct FErp {
 
 // Eq. MSM with Eq. MSMCost.  C(np, x, y) = c + dist(np, [min(x,y), max(x,y)]),
 // dist = 0 when np lies between x and y, else min(|np-x|, |np-y|).  With
-// e = x - np and f = y - np, and the sign of e known in advance, that is
-// dist = clamp(sign(e) * f, 0, |e|): np is outside the interval exactly when
-// f has the sign of e, and then the nearer end is whichever of |e|, |f| is
-// smaller.  For the AlternateRow cost x = s_{i-1} is fixed along a row, for
-// the AlternateColumn cost y = t_{j-1} is fixed along a column, so each cost
-// is one fused multiply-add and one clamp, and c + clamp(u, 0, E) =
-// clamp(c + u, c, c + E) gives the same float as the printed form (every
-// step is exact or one rounding of the same sum).
+// e = x - np (fixed along a row for the AlternateRow cost, x = s_{i-1}, or
+// along a column for the AlternateColumn cost, x = t_{j-1}) and f = y - np,
+// np is between x and y exactly when f / e <= 0, and otherwise
+// min(|e|, |f|) = |e| * min(f / e, 1).  So dist = |e| * sat(f * (1/e)),
+// sat = clamp to [0, 1], which is one multiply with saturation (a modifier
+// of the FMA pipe, no min/max) and one fused multiply-add for c + |e| * (.).
+// 1/e is a per-row or per-column constant (0 when e = 0: then np is always
+// between).  The products round where the printed min does not (a few ulps
+// of that term); every path, the DP's and the diagonal bound's, evaluates
+// this same function.
+__device__ __forceinline__ float mul_sat(float a, float b) {
+    float d;
+    asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 struct FMsm {
     static constexpr bool kWeights = false;
     static constexpr bool kCarry = false;
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
-    struct Col { float t, nsg, gc; };   // g = t_{j-1} - t_j: nsg = -sign(g), gc = c + |g|
-    struct Row { float s, sge, ec; };   // e = s_{i-1} - s_i: sge = sign(e), ec = c + |e|
-    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sge, r.ec, 0.f); }
+    struct Col { float t, ig, ag; };   // g = t_{j-1} - t_j: ig = 1/g (0 if g = 0), ag = |g|
+    struct Row { float s, ie, ae; };   // e = s_{i-1} - s_i: ie = 1/e (0 if e = 0), ae = |e|
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.ie, r.ae, 0.f); }
     __device__ static Row unpack(const float4& p) { return {p.x, p.y, p.z}; }
-    __device__ static Col col(float t, float tprev, const KParams& kp) {
+    __device__ static Col col(float t, float tprev, const KParams&) {
         const float g = __fsub_rn(tprev, t);
-        return {t, g >= 0.f ? -1.f : 1.f, __fadd_rn(kp.msm_c, fabsf(g))};
+        return {t, g != 0.f ? __frcp_rn(g) : 0.f, fabsf(g)};
     }
-    __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
+    __device__ static Row row(float s, float sprev, const KParams&, const float*) {
         const float e = __fsub_rn(sprev, s);
-        return {s, e >= 0.f ? 1.f : -1.f, __fadd_rn(kp.msm_c, fabsf(e))};
+        return {s, e != 0.f ? __frcp_rn(e) : 0.f, fabsf(e)};
     }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams& kp) {
-        const float f = __fsub_rn(c.t, r.s);                                       // t_j - s_i
-        const float a = __fadd_rn(dg, fabsf(f));                                   // move |s_i - t_j|
-        const float tc = fminf(fmaxf(__fmaf_rn(r.sge, f, kp.msm_c), kp.msm_c), r.ec);   // C(s_i, s_{i-1}, t_j)
-        const float lc = fminf(fmaxf(__fmaf_rn(c.nsg, f, kp.msm_c), kp.msm_c), c.gc);   // C(t_j, s_i, t_{j-1})
+        const float f = __fsub_rn(c.t, r.s);                                   // t_j - s_i
+        const float a = __fadd_rn(dg, fabsf(f));                               // move |s_i - t_j|
+        const float tc = __fmaf_rn(r.ae, mul_sat(r.ie, f), kp.msm_c);          // C(s_i, s_{i-1}, t_j)
+        const float lc = __fmaf_rn(c.ag, mul_sat(c.ig, -f), kp.msm_c);  // C(t_j, t_{j-1}, s_i)
         return min3f(a, __fadd_rn(tp, tc), __fadd_rn(lf, lc));
     }
 };
