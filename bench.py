@@ -47,13 +47,13 @@ KIND_PARAMS = {
 OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 9, "twe": 7}
 # Kernels this library launches per eap_nn1 call: init, upper bound, sort,
 # DP, unpack; ERP adds two border kernels, WDTW one weight table.
-LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 7, "msm": 5, "twe": 5}
+LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 8, "msm": 6, "twe": 6}
 N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # DRAM bytes (read + write) of the dominant DP launch on this workload, from
 # one ncu capture (profiles/dp_kernel_msm_nn1_512_traffic.md), valid only for
 # the library build whose source fingerprint is recorded with it.
-TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 8783360,
-           "fingerprint": "210d80eba8c904facb4730f6870afd948ba2d848cf4e9e41103846706d50bb28"}
+TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 14839040,
+           "fingerprint": "6fa9a3b8396dd4eb9a71e0467fe5434cacdc8efa335048b4dad347406d76ce5c"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
