@@ -52,6 +52,8 @@ N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # DRAM bytes (read + write) of the dominant DP launch on this workload, from
 # one ncu capture (profiles/dp_kernel_msm_nn1_512_traffic.md), valid only for
 # the library build whose source fingerprint is recorded with it.
+# The EAPruned DP launch of this workload (L = 512): 16 lanes per pair, W = 4.
+DP_KERNEL = "group_dp_kernel<{}, W=4, G=16>"
 TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 14839040,
            "fingerprint": "6fa9a3b8396dd4eb9a71e0467fe5434cacdc8efa335048b4dad347406d76ce5c"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
@@ -391,11 +393,11 @@ def main():
     traffic = None
     try:
         from paper_2102_05221_gb300 import build as _b
-        if TRAFFIC["kernel"] == f"dp_kernel<{dom}>" and TRAFFIC["fingerprint"] == _b._fingerprint():
+        if TRAFFIC["kernel"] == DP_KERNEL.format(dom) and TRAFFIC["fingerprint"] == _b._fingerprint():
             traffic = TRAFFIC["bytes"]
     except Exception:
         traffic = None
-    roofline = {"bound": "alu", "kernel": f"dp_kernel<{dom}>", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "alu", "kernel": DP_KERNEL.format(dom), "achieved": achieved, "peak": peak,
                 "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "work_basis": f"{OPS_PER_CELL[dom]} FP32 ops per computed cell"}

@@ -365,8 +365,28 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
     }
     // Base and EABase compute (nearly) every cell: wide strips.
     if (prune != kPmPruned) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
-    if (kind == EAP_TWE && max_cols > 128) return 8;
+    // TWE's 7-op cell amortises the per-step work better at W = 8 when the
+    // 16-lane groups (W = 4) do not apply.
+    if (kind == EAP_TWE && max_cols > 2048) return 8;
     return 4;
+}
+
+// Lanes per pair for the EAPruned DP: 8 or 16 (group_dp_kernel, several pairs
+// per warp) or 0 (a warp per pair).  EAP_G overrides (8, 16, or 32 = warp).
+// Groups keep one boundary column per group in shared memory, so they are
+// limited to rows <= 2048 (16 lanes) and <= 1024 (8 lanes), and to W = 4, 8.
+// Default: 16 lanes at W = 4 (measured on the 1000 x 1000 x 512 workload:
+// 9-17% less DP time than a warp per pair for every distance; 8 lanes and
+// W = 8 groups were slower).
+int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
+    (void)kind; (void)cost; (void)max_cols;
+    if (prune != kPmPruned || (W != 4 && W != 8)) return 0;
+    int g = W == 4 ? 16 : 0;
+    const char* e = std::getenv("EAP_G");
+    if (e) g = std::atoi(e);
+    if (g == 8 && max_rows <= 1024) return 8;
+    if (g == 16 && max_rows <= 2048) return 16;
+    return 0;
 }
 
 // DP launch bracketed by CUDA events on the call's stream when timing is asked.
@@ -575,6 +595,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.max_rows = mq;
     c.max_cols = mr;
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
+    c.group = c.cta ? 0 : choose_group(p->kind, cost, mq, mr, c.prune, c.W);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -830,6 +851,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.max_rows = mx;
         c.max_cols = mx;
         c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
+        c.group = c.cta ? 0 : choose_group(p->kind, cost, mx, mx, c.prune, c.W);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -921,6 +943,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.max_rows = ma;
     c.max_cols = mb;
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
+    c.group = c.cta ? 0 : choose_group(p->kind, cost, ma, mb, c.prune, c.W);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1090,6 +1113,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
+    c.group = choose_group(p->kind, cost, ma, mb, c.prune, c.W);
     c.stream = st;
     if ((e = dispatch(c, false))) return cuda_status(e);
     if (opt_stats) {
@@ -1140,6 +1164,9 @@ void map_set(int kind, int cost, int bucket, int m) {
 int pick_w(int kind, int cost, int max_cols, int prune) { return choose_w(kind, cost, max_cols, prune); }
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
     return choose_cta(kind, cost, max_rows, max_cols, prune);
+}
+int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
+    return choose_group(kind, cost, max_rows, max_cols, prune, W);
 }
 int bucket_of(int len) { return length_bucket(len); }
 int resolve_cost_ext(const eap_params* p) { return resolve_cost(p); }

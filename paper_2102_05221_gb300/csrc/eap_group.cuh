@@ -1,0 +1,340 @@
+// eap_group.cuh -- EAPruned DP with G = 8 or 16 lanes per pair (32/G pairs per
+// warp), for series short enough that pruning granularity, not per-step
+// overhead, decides the cost.
+//
+// The skewed wavefront of a pair is a staircase whose cells span about
+// lanes x (W + 1) diagonals; everything the pair computes is the union of
+// those staircases over the panel, so a narrower staircase wastes fewer
+// cells outside the band of live cells (left of the first live row and
+// right of the pruning point).  A G-lane group halves or quarters the span
+// of the warp-per-pair mapping at the same strip width W.
+//
+// The groups of a warp run different pairs, so their panels start and end at
+// different times.  To keep the warp converged, the kernel is one flat loop:
+// (1) each group that needs a new pair or a new panel sets it up (divergent,
+// group-local collectives only), (2) the warp re-converges and runs U
+// wavefront steps in lock-step, every lane predicated by its own group's
+// state, (3) one ballot gives each group its frontier vote, and groups whose
+// panel ended process its end (divergent).  The arithmetic of a cell, the
+// pruning rules and the results are those of warp_pair in the EAPruned mode.
+#pragma once
+
+#include "eap_device.cuh"
+
+namespace eapd {
+
+#ifndef EAP_GROUP_ROUNDS
+#define EAP_GROUP_ROUNDS 2
+#endif
+// Register-rotation cycles (W + 1 steps each) per lock-step round.
+constexpr int kGroupRounds = EAP_GROUP_ROUNDS;
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+template <class F, int W, int G, bool WIN>
+__global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, const KParams kp) {
+    static_assert(G == 8 || G == 16, "group width");
+    constexpr int P = G * W;                 // columns per panel
+    constexpr int NG = 32 / G;               // groups per warp
+    constexpr int U = kGroupRounds * (W + 1);   // steps per round (the strip registers rotate back every W + 1)
+    enum { kNeedPair = 0, kNeedPanel = 1, kStep = 2, kDone = 3 };
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);           // lane within the group
+    const unsigned gmask = group_mask<G>(lane);
+    float* bnd = smem + ((threadIdx.x >> 5) * NG + lane / G) * job.bnd_stride;
+    unsigned long long cells = 0, npairs = 0, nab = 0, nlb = 0;
+
+    int state = kNeedPair;
+    // Pair state (uniform within the group).
+    PairIn in;
+    in.A = in.B = in.bA = in.bB = in.wt = nullptr;
+    in.rp = nullptr;
+    in.cut_src = nullptr;
+    in.La = in.Lb = 0;
+    in.w = 0;
+    in.cut = EAP_FINF;
+    unsigned long long item = 0;
+    int ai = 0, bi = 0, npan = 0, p = 0, blo = 1, bhi = 0;
+    float cut = EAP_FINF;
+    // Panel state.
+    int cf = 0, cl = 0, r0 = 1, r1 = 0, t = 0, nsteps = 0, c0 = 0, nvalid = 0;
+    bool last = false, lane_out = true, stG = false;
+    typename F::Col cc[W];
+    float v[W], wr[W], cy[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) { v[u] = EAP_FINF; wr[u] = 0.f; cy[u] = 0.f; cc[u] = F::col(0.f, 0.f, kp); }
+    float dg = EAP_FINF, sp = 0.f, s_next = 0.f;
+    float4 pk_next = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // The group leader publishes a pair's result.
+    auto finish_pair = [&](float d, bool ab) {
+        if (gl == 0) {
+            ++npairs;
+            nab += ab ? 1 : 0;
+            if (job.mode == kModeNN1) {
+                if (d != EAP_FINF) atomicMin(job.best + ai, pack_best(d, (unsigned)bi));
+            } else if (job.mode == kModePairwise) {
+                const int n = job.A.n;
+                job.out[(size_t)ai * n + bi] = d;
+                job.out[(size_t)bi * n + ai] = d;
+            } else {
+                job.out[item] = d;
+            }
+        }
+        __syncwarp(gmask);
+        state = kNeedPair;
+    };
+
+    auto begin_pair = [&]() {
+        unsigned long long it = 0;
+        if (gl == 0) it = atomicAdd(job.counter, 1ULL);
+        it = __shfl_sync(gmask, it, 0, G);
+        if (it >= job.nitems) { state = kDone; return; }
+        item = it;
+        const unsigned long long* cut_src = nullptr;
+        float c = EAP_FINF;
+        if (job.mode == kModeNN1) {
+            const unsigned long long rank = item / (unsigned)job.A.n;
+            ai = (int)(item - rank * (unsigned)job.A.n);
+            bi = job.order ? __ldg(job.order + (size_t)ai * job.B.n + rank) : (int)rank;
+            if (job.cut) {
+                c = __ldg(job.cut + (size_t)ai * job.B.n + bi);   // the pair's own bound (Prune)
+            } else {
+                cut_src = job.best + ai;
+                unsigned long long cv = 0;
+                if (gl == 0) cv = *(volatile const unsigned long long*)cut_src;
+                cv = __shfl_sync(gmask, cv, 0, G);
+                c = __uint_as_float((unsigned)(cv >> 32));
+                if (job.lb && __ldg(job.lb + (size_t)ai * job.B.n + bi) > c) {   // Alg. 2
+                    if (gl == 0) ++nlb;
+                    return;   // still kNeedPair
+                }
+            }
+        } else if (job.mode == kModePairwise) {
+            tri_decode(item, job.A.n, ai, bi);
+            if (job.cut) c = __ldg(job.cut + item);
+        } else {
+            ai = __ldg(job.ia + item);
+            bi = __ldg(job.ib + item);
+            if (job.cut) c = __ldg(job.cut + item);
+        }
+        const int64_t oa = __ldg(job.A.off + ai), ob = __ldg(job.B.off + bi);
+        in.A = job.A.data + oa;
+        in.B = job.B.data + ob;
+        in.La = __ldg(job.A.len + ai);
+        in.Lb = __ldg(job.B.len + bi);
+        in.bA = job.A.border ? job.A.border + oa : nullptr;
+        in.bB = job.B.border ? job.B.border + ob : nullptr;
+        in.wt = job.wdtw_table ? job.wdtw_table + kWdtwOff - max(in.La, in.Lb) : nullptr;
+        in.rp = job.rowpack ? job.rowpack + oa : nullptr;
+        in.cut_src = cut_src;
+        in.w = pair_window(kp, in.La, in.Lb);
+        in.cut = c;
+        cut = c;
+        if (in.w < abs(in.La - in.Lb)) { finish_pair(EAP_FINF, true); return; }   // no alignment in the window
+        npan = (in.Lb + P - 1) / P;
+        p = 0;
+        // Left boundary of panel 0: the vertical border M(r, 0) (ERP), else +inf.
+        blo = 1;
+        bhi = 0;
+        if (F::kBorders) {
+            const int vmax = min(in.La, in.w + 1);
+            int live = 0;
+            for (int rr = 1; rr <= vmax; rr += G) {
+                const int r = rr + gl;
+                const float x = r <= vmax ? __ldg(in.bA + r - 1) : EAP_FINF;
+                if (r <= vmax) bnd[r] = x;
+                live += __popc(__ballot_sync(gmask, r <= vmax && x <= cut));
+            }
+            if (live > 0) { blo = 1; bhi = live; }   // the border increases: live rows are a prefix
+        }
+        __syncwarp(gmask);
+        state = kNeedPanel;
+    };
+
+    auto begin_panel = [&]() {
+        const int La = in.La, Lb = in.Lb, w = in.w;
+        cf = p * P + 1;
+        cl = min(cf + P - 1, Lb);
+        last = (p == npan - 1);
+        if (in.cut_src) {
+            unsigned long long cv = 0;
+            if (gl == 0) cv = *(volatile const unsigned long long*)in.cut_src;
+            cv = __shfl_sync(gmask, cv, 0, G);
+            cut = fminf(cut, __uint_as_float((unsigned)(cv >> 32)));
+        }
+        const bool top_live = hborder<F>(in, cf - 1) <= cut;
+        if (!top_live && blo > bhi) { finish_pair(EAP_FINF, true); return; }
+        r0 = top_live ? 1 : blo;
+        r1 = La;
+        if (WIN) { r0 = max(r0, cf - w); r1 = min(La, cl + w); }
+        if (r0 > r1) {
+            if (last) { finish_pair(EAP_FINF, true); return; }
+            blo = 1;
+            bhi = 0;
+            ++p;
+            return;   // still kNeedPanel
+        }
+        for (int r = r0 + gl; r <= r1; r += G)
+            if (r < blo || r > bhi) bnd[r] = EAP_FINF;
+        __syncwarp(gmask);
+        c0 = cf + gl * W;
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const int c = c0 + u;
+            const float tv = c <= Lb ? __ldg(in.B + c - 1) : kPadValue;
+            const float tprev = c == 1 ? 0.f : (c - 1 <= Lb ? __ldg(in.B + c - 2) : kPadValue);
+            cc[u] = F::col(tv, tprev, kp);
+            v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
+        }
+        init_weights<F, W>(wr, in.wt, kp, r0, c0);
+        {
+            const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if constexpr (F::kCarry) cy[u] = F::carry_init(s_before, cc[u]);
+                else cy[u] = 0.f;
+            }
+        }
+        if (r0 == 1) dg = hborder<F>(in, c0 - 1 <= Lb ? c0 - 1 : Lb + 1);
+        else dg = (gl == 0) ? bnd[r0 - 1] : EAP_FINF;
+        lane_out = c0 > Lb;
+        nvalid = max(0, min(W, Lb - c0 + 1));
+        stG = !last && gl == G - 1;
+        if constexpr (F::kPacked) {
+            pk_next = __ldg(in.rp + r0 - 1);
+        } else {
+            sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
+            s_next = __ldg(in.A + r0 - 1);
+        }
+        nsteps = r1 - r0 + G;
+        t = 0;
+        state = kStep;
+    };
+
+    // End of the current panel after `done` steps.
+    auto end_panel = [&](int done) {
+        const int La = in.La, Lb = in.Lb;
+        {
+            const int lastrow = min(r1, r0 + done - 1 - gl);
+            if (lastrow >= r0) cells += (unsigned long long)(lastrow - r0 + 1) * (unsigned)nvalid;
+        }
+        __syncwarp(gmask);
+        if (last) {
+            const int off = Lb - cf;         // offset of column Lb inside the panel
+            const int lr = off / W, ur = off % W;
+            float res = EAP_FINF;
+#pragma unroll
+            for (int u = 0; u < W; ++u) if (u == ur) res = v[u];
+            res = __shfl_sync(gmask, res, lr, G);
+            const int lastrow = min(r1, r0 + done - 1 - lr);
+            if (lastrow != La) res = EAP_FINF;
+            if (!(res <= cut)) res = EAP_FINF;
+            finish_pair(res, res == EAP_FINF);
+            return;
+        }
+        // Live rows of the column handed to the next panel.
+        const int wlast = min(r1, r0 + done - 1 - (G - 1));
+        int lo = 0x7fffffff, hi = -1;
+        for (int r = r0 + gl; r <= wlast; r += G) {
+            if (bnd[r] <= cut) { lo = min(lo, r); hi = max(hi, r); }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(gmask, lo, o, G));
+            hi = max(hi, __shfl_xor_sync(gmask, hi, o, G));
+        }
+        if (hi < 0) { blo = 1; bhi = 0; } else { blo = lo; bhi = hi; }
+        __syncwarp(gmask);
+        ++p;
+        state = kNeedPanel;
+    };
+
+    // One wavefront step for every group, predicated by each lane's state
+    // (CHECK) or, when every lane of the warp is inside its panel's rows for
+    // the whole round, unpredicated.
+    auto step = [&](int tt, auto check) {
+        constexpr bool kCheck = decltype(check)::value;
+        const int row = r0 + tt - gl;
+        const bool act = kCheck ? (state == kStep && row >= r0 && row <= r1) : true;
+        const float bv = act ? bnd[row] : EAP_FINF;
+        float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1, G);
+        if (gl == 0) x = bv;
+        if (act) {
+            typename F::Row rc;
+            if constexpr (F::kPacked) {
+                rc = F::unpack(pk_next);
+                pk_next = __ldg(in.rp + row);   // row <= La: the entry past La is readable
+            } else {
+                const float s = s_next;
+                s_next = __ldg(in.A + min(row, in.La - 1));
+                rc = F::row(s, sp, kp, in.wt);
+                sp = s;
+            }
+            shift_weights<F, W>(wr, in.wt, kp, row, c0);
+            strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, in.w, kp);
+            dg = x;
+            if (stG) bnd[row] = v[W - 1];
+        }
+    };
+
+    for (;;) {
+        // (1) Set-up, per group; every pass consumes a work item or a panel.
+        while (state == kNeedPair || state == kNeedPanel) {
+            if (state == kNeedPair) begin_pair();
+            else begin_panel();
+        }
+        __syncwarp();
+        if (__ballot_sync(EAP_FULL, state == kStep) == 0u) break;   // every group is done
+        // (2) U lock-step wavefront steps; unpredicated when every group is
+        // stepping with all its lanes inside the panel's rows (no ramp).
+        const bool steady = __all_sync(EAP_FULL, state == kStep && t >= G - 1 && t + U <= r1 - r0 + 1);
+        if (steady) {
+#pragma unroll
+            for (int k = 0; k < U; ++k) step(t + k, BoolC<false>{});
+        } else {
+#pragma unroll
+            for (int k = 0; k < U; ++k) step(t + k, BoolC<true>{});
+        }
+        // (3) Frontier vote: every cell a later row of this panel could depend
+        // on (each lane's strip and left input, the group's first lane's
+        // unread boundary rows) is above the cut-off.
+        bool dead = true;
+        if (state == kStep) {
+            const int row = r0 + t + U - 1 - gl;
+            if (row <= r1 && !lane_out) {
+                float m = dg;
+#pragma unroll
+                for (int u = 0; u < W; ++u) m = fminf(m, v[u]);
+                dead = m > cut;
+                if (gl == 0 && row < bhi) dead = false;
+            }
+        }
+        const bool gdead = (__ballot_sync(EAP_FULL, dead) & gmask) == gmask;
+        if (state == kStep) {
+            t += U;
+            if (gdead || t >= nsteps) end_panel(gdead ? t : nsteps);
+        }
+    }
+    if (job.stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cells += __shfl_xor_sync(EAP_FULL, cells, o);
+            npairs += __shfl_xor_sync(EAP_FULL, npairs, o);
+            nab += __shfl_xor_sync(EAP_FULL, nab, o);
+            nlb += __shfl_xor_sync(EAP_FULL, nlb, o);
+        }
+        if (lane == 0) {
+            if (npairs) atomicAdd(job.stats + kStatPairs, npairs);
+            if (nab) atomicAdd(job.stats + kStatAbandoned, nab);
+            if (cells) atomicAdd(job.stats + kStatCells, cells);
+            if (nlb) atomicAdd(job.stats + kStatLbPruned, nlb);
+        }
+    }
+}
+
+}  // namespace eapd

@@ -19,6 +19,7 @@ struct LaunchCtx {
     int W;               // strip width per lane (4, 8 or 16)
     int prune;           // 1 EAPruned, 0 Base, 2 EABase (eapd::kPm*)
     float4* rowpack;     // scratch of A.data_len + 1 float4 for the packed row constants (ERP, MSM, TWE)
+    int group;           // EAPruned with 8 or 16 lanes per pair (group_dp_kernel); 0 = a warp per pair
     int sms;             // multiprocessors of the device
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
@@ -47,6 +48,7 @@ void tune_reset();
 void map_set(int kind, int cost, int bucket, int m);   // 0 untuned, 1 warp, 2 CTA
 int pick_w(int kind, int cost, int max_cols, int prune);
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
+int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).
@@ -92,6 +94,30 @@ int run_dp(const LaunchCtx& c) {
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     unsigned long long grid = (unsigned long long)per_sm * c.sms;
     const unsigned long long need = (c.job.nitems + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kThreads, smem, c.stream>>>(c.job, c.kp);
+    return (int)cudaGetLastError();
+}
+
+// G-lane groups (32/G pairs per warp), EAPruned only; one boundary column per group.
+template <class F, int W, int G, bool WIN>
+int run_group(const LaunchCtx& c) {
+    using namespace eapd;
+    void (*kern)(const DPJob, const KParams) = group_dp_kernel<F, W, G, WIN>;
+    const size_t smem = (size_t)kWarpsPerBlock * (32 / G) * c.job.bnd_stride * sizeof(float);
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    unsigned long long grid = (unsigned long long)per_sm * c.sms;
+    const unsigned long long per_block = (unsigned long long)kWarpsPerBlock * (32 / G);
+    const unsigned long long need = (c.job.nitems + per_block - 1) / per_block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kThreads, smem, c.stream>>>(c.job, c.kp);
@@ -166,6 +192,10 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
         const int e = run_rowpack<F>(c);
         if (e) return e;
         d.job.rowpack = c.rowpack;
+    }
+    if (c.group && c.prune == eapd::kPmPruned && (c.W == 4 || c.W == 8)) {
+        if (c.group == 8) return c.W == 4 ? run_group<F, 4, 8, WIN>(d) : run_group<F, 8, 8, WIN>(d);
+        if (c.group == 16) return c.W == 4 ? run_group<F, 4, 16, WIN>(d) : run_group<F, 8, 16, WIN>(d);
     }
     switch (c.W) {
         case 4: return run_dp<F, 4, WIN>(d);

@@ -239,3 +239,4 @@ __global__ void __launch_bounds__(32 * kUbTileWarps) ub_tile_kernel(const DPJob 
 }  // namespace eapd
 
 #include "eap_cta.cuh"
+#include "eap_group.cuh"

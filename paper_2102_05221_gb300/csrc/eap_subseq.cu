@@ -509,6 +509,7 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
             c.max_rows = m;
             c.max_cols = m;
             c.cta = eaph::pick_cta(p->kind, cost, m, m, kPmPruned);
+            c.group = c.cta ? 0 : eaph::pick_group(p->kind, cost, m, m, kPmPruned, c.W);
             c.stream = st;
             e |= p->kind == EAP_DTW ? eaph::launch_dp_dtw(c, false) : eaph::launch_dp_cdtw(c, false);
         }
