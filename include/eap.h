@@ -118,6 +118,12 @@ typedef struct {
     double   dp_ms;            /* device time of the DP kernel launch(es), CUDA events on the call's stream */
 } eap_stats;
 
+/* Inputs must be finite.  Validation mode -- the environment variable
+ * EAP_CHECK_INPUTS=1 -- makes every entry point scan its input series for
+ * NaN / Inf first (after a device-wide synchronisation, so not inside a
+ * stream capture) and return EAP_EINVAL if it finds any; otherwise non-finite
+ * values are not detected and give unspecified results. */
+
 /* ---- entry points -------------------------------------------------------- */
 
 /* 1-NN search (Alg. 1, each distance evaluation Alg. 5 with the query's

@@ -288,6 +288,43 @@ int validate_params(const eap_params* p) {
     return EAP_OK;
 }
 
+// Validation mode (EAP_CHECK_INPUTS=1 in the environment): input series are
+// scanned for NaN / Inf before any work, after a device-wide synchronisation
+// (so data produced on any stream is complete), on the legacy stream.
+__device__ unsigned g_nonfinite_flag;
+
+__global__ void nonfinite_kernel(const float* __restrict__ data, const int64_t* __restrict__ off,
+                                 const int32_t* __restrict__ len, int n, long long span) {
+    // n series at (off, len), or, with off == nullptr, one run of `span` values.
+    const int count = off ? n : 1;
+    for (int s = blockIdx.x; s < count; s += gridDim.x) {
+        const float* x = off ? data + off[s] : data;
+        const long long L = off ? (long long)len[s] : span;
+        bool bad = false;
+        for (long long i = threadIdx.x; i < L; i += blockDim.x) bad |= !isfinite(__ldg(x + i));
+        if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&g_nonfinite_flag, 1u);
+    }
+}
+
+bool check_inputs_enabled() {
+    const char* e = std::getenv("EAP_CHECK_INPUTS");
+    return e && e[0] && e[0] != '0';
+}
+
+// EAP_OK when every value is finite, EAP_EINVAL otherwise, EAP_EDEVICE on a CUDA error.
+int check_finite(const float* data, const int64_t* off, const int32_t* len, int n, long long span) {
+    if ((off && n <= 0) || (!off && span <= 0)) return EAP_OK;
+    const unsigned zero = 0;
+    unsigned flag = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EAP_EDEVICE;
+    if (cudaMemcpyToSymbol(g_nonfinite_flag, &zero, sizeof(zero)) != cudaSuccess) return EAP_EDEVICE;
+    const int blocks = off ? std::min(n, 4096) : 1;
+    nonfinite_kernel<<<blocks, 256>>>(data, off, len, n, span);
+    if (cudaGetLastError() != cudaSuccess) return EAP_EDEVICE;
+    if (cudaMemcpyFromSymbol(&flag, g_nonfinite_flag, sizeof(flag)) != cudaSuccess) return EAP_EDEVICE;
+    return flag ? EAP_EINVAL : EAP_OK;
+}
+
 int validate_set(const eap_series_set* s, int* max_len) {
     if (!s || s->count < 0) return EAP_EINVAL;
     int mx = 0;
@@ -300,6 +337,7 @@ int validate_set(const eap_series_set* s, int* max_len) {
         if (L > mx) mx = L;
     }
     *max_len = mx;
+    if (check_inputs_enabled()) return check_finite(s->data, s->offsets, s->lengths, s->count, 0);
     return EAP_OK;
 }
 
@@ -1171,6 +1209,9 @@ int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W)
 int bucket_of(int len) { return length_bucket(len); }
 int resolve_cost_ext(const eap_params* p) { return resolve_cost(p); }
 int validate_set_ext(const eap_series_set* s, int* max_len) { return validate_set(s, max_len); }
+int check_finite_run(const float* data, long long n) {
+    return check_inputs_enabled() ? check_finite(data, nullptr, nullptr, 0, n) : EAP_OK;
+}
 }  // namespace eaph
 
 // Launch helpers for the batched path (eap_batch.cu), wrapping the kernels above.

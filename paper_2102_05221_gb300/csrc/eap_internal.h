@@ -39,6 +39,8 @@ int nn1_device(const ::eap_params* p, const ::eap_series_set* queries, const ::e
 // Parameter validation shared with the serving loop; returns an EAP_* code.
 int validate_params_ext(const ::eap_params* p);
 int validate_set_ext(const ::eap_series_set* s, int* max_len);
+// Validation mode only (EAP_CHECK_INPUTS): EAP_EINVAL if data[0..n) holds a NaN or Inf.
+int check_finite_run(const float* data, long long n);
 int resolve_cost_ext(const ::eap_params* p);
 
 // Strip-width table filled by the autotuner (eap_api.cu).

@@ -379,6 +379,7 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
     int mq = 0;
     if ((rc = eaph::validate_set_ext(queries, &mq))) return rc;
     if (n < 0 || n >= (1LL << 31) || (n > 0 && !ref)) return EAP_EINVAL;
+    if ((rc = eaph::check_finite_run(ref, n))) return rc;
     if (queries->count > 0 && (!out_pos || !out_dist)) return EAP_EINVAL;
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     const int nq = queries->count;

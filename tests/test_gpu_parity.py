@@ -212,3 +212,30 @@ def test_nn1_with_lb_keogh_cascade(eap, kind, lb):
     assert s1["pairs_lb_pruned"] > 0 and s0["pairs_lb_pruned"] == 0
     D = O.cross(oracle_params(kind, **kw), te, tr)
     check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
+
+
+def test_validation_mode_rejects_non_finite_inputs(eap):
+    """EAP_CHECK_INPUTS=1 scans the inputs for NaN / Inf first."""
+    import os
+    x = synth.ragged_walks(4, [50] * 4, 91)
+    bad = synth.pack([x.series(0), np.where(np.arange(50) == 7, np.nan, x.series(1)).astype(np.float32)])
+    Q, B = eap.SeriesSet.from_packed(x), eap.SeriesSet.from_packed(bad)
+    T = np.concatenate([x.series(0), [np.inf], x.series(1)]).astype(np.float32)
+    old = os.environ.get("EAP_CHECK_INPUTS")
+    os.environ["EAP_CHECK_INPUTS"] = "1"
+    try:
+        for call in (lambda: eap.eap_nn1(eap.params("dtw"), Q, B),
+                     lambda: eap.eap_pairs(eap.params("msm"), B, Q, [1], [0], [1.0]),
+                     lambda: eap.eap_pairwise(eap.params("erp"), B),
+                     lambda: eap.eap_subseq(eap.params("cdtw"), T, Q)):
+            with pytest.raises(eap.EapError) as e:
+                call()
+            assert e.value.code == eap.EAP_EINVAL
+        # Finite inputs pass the scan.
+        idx, dist = eap.eap_nn1(eap.params("dtw"), Q, Q)
+        assert np.array_equal(idx.cpu().numpy(), np.arange(4))
+    finally:
+        if old is None:
+            del os.environ["EAP_CHECK_INPUTS"]
+        else:
+            os.environ["EAP_CHECK_INPUTS"] = old
