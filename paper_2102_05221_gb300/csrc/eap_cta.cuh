@@ -91,7 +91,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     bool wrote_live = false;   // this lane handed a live boundary row to its consumer during this tick
     typename F::Col cc[W];
     float v[W], cy[W], wr[W];
-    float dg = EAP_FINF, sp = 0.f, s_next = 0.f;
+    float dg = EAP_FINF, sp = 0.f, s_next = 0.f, fd = 0.f;
     bool lane_out = false;
 
     auto left_in = [&](int row) -> float {   // lane 0's left input at `row` of panel p
@@ -130,7 +130,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                     v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
                 }
                 const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
-                init_weights<F, W>(wr, in.wt, kp, r0, c0);
+                init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     if constexpr (F::kCarry) cy[u] = F::carry_init(s_before, cc[u]);
@@ -155,7 +155,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                         const float s = s_next;
                         s_next = __ldg(in.A + min(row, La - 1));
                         const typename F::Row rc = F::row(s, sp, kp, in.wt);
-                        shift_weights<F, W>(wr, in.wt, kp, row, c0);
+                        shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
                         strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                         sp = s;
                         dg = x;

@@ -245,8 +245,9 @@ struct FTwe {
     __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
         return {s, sprev, __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda)};
     }
-    // 2 nu |i - j| for a cell with i - j = d.
+    // 2 nu |i - j| for a cell with i - j = d (an integer, or its exact float).
     __device__ static float pen(const KParams& kp, int d) { return __fmul_rn(kp.twe_nu2, (float)abs(d)); }
+    __device__ static float pen_f(const KParams& kp, float d) { return __fmul_rn(kp.twe_nu2, fabsf(d)); }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int dij, float,
                                  const KParams& kp) {
         const float gm0 = __fadd_rn(pcost<COST>(r.s, c.t), pcost<COST>(r.sprev, c.tprev));
@@ -323,19 +324,28 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const f
 }
 
 // Per-cell diagonal factors of a strip (WDTW weights, TWE penalties) for the
-// next row: wr[u] <- wr[u-1], wr[0] <- the factor of i - j = row - c0.
+// next row: wr[u] <- wr[u-1], wr[0] <- the factor of i - j = row - c0.  For
+// TWE, fd holds row - 1 - c0 as a float (an exact integer) and steps by one
+// per row, so the penalty of the new cell needs no integer conversion.
 template <class F, int W>
-__device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, const KParams& kp, int row, int c0) {
+__device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, const KParams& kp, int row, int c0,
+                                              float& fd) {
     if constexpr (F::kWeights || F::kPen) {
 #pragma unroll
         for (int u = W - 1; u > 0; --u) wr[u] = wr[u - 1];
-        if constexpr (F::kWeights) wr[0] = __ldg(wt + 2 * abs(row - c0));
-        else wr[0] = F::pen(kp, row - c0);
+        if constexpr (F::kWeights) {
+            wr[0] = __ldg(wt + 2 * abs(row - c0));
+        } else {
+            fd = __fadd_rn(fd, 1.f);
+            wr[0] = F::pen_f(kp, fd);
+        }
     }
 }
 // Factors before a strip's first row r0: those of i - j = r0 - 1 - (c0 + u).
 template <class F, int W>
-__device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, const KParams& kp, int r0, int c0) {
+__device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, const KParams& kp, int r0, int c0,
+                                             float& fd) {
+    fd = (float)(r0 - 1 - c0);
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         if constexpr (F::kWeights) wr[u] = __ldg(wt + 2 * abs(r0 - 1 - c0 - u));
@@ -435,8 +445,9 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
             cc[u] = F::col(t, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
-        float wr[W];   // weights of the strip's cells for the current row (WDTW)
-        init_weights<F, W>(wr, in.wt, kp, r0, c0);
+        float wr[W];   // diagonal factors of the strip's cells for the current row (WDTW, TWE)
+        float fd;      // row - 1 - c0 as a float (TWE)
+        init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
         float cy[W];   // carried per-cell values of the previous row (TWE)
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
@@ -485,7 +496,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                     rc = F::row(s, sp, kp, in.wt);
                     sp = s;
                 }
-                shift_weights<F, W>(wr, in.wt, kp, row, c0);
+                shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
                 strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                 dg = x;
                 if (st31) {

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
     float v[W], wr[W], cy[W];
 #pragma unroll
     for (int u = 0; u < W; ++u) { v[u] = EAP_FINF; wr[u] = 0.f; cy[u] = 0.f; cc[u] = F::col(0.f, 0.f, kp); }
-    float dg = EAP_FINF, sp = 0.f, s_next = 0.f;
+    float dg = EAP_FINF, sp = 0.f, s_next = 0.f, fd = 0.f;
     float4 pk_next = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // The group leader publishes a pair's result.
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
             cc[u] = F::col(tv, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
-        init_weights<F, W>(wr, in.wt, kp, r0, c0);
+        init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
 #pragma unroll
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
                 rc = F::row(s, sp, kp, in.wt);
                 sp = s;
             }
-            shift_weights<F, W>(wr, in.wt, kp, row, c0);
+            shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
             strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, in.w, kp);
             dg = x;
             if (stG) bnd[row] = v[W - 1];
