@@ -43,6 +43,12 @@ struct CtaShared {
     unsigned long long item;
 };
 
+// Packed row constants in the CTA wavefront: MSM gains (one load instead of
+// the per-row reciprocals); TWE, whose carried costs already hold many
+// registers, is measured faster computing them per row.
+template <class F>
+constexpr bool kCtaPacked = F::kPacked && !F::kCarry;
+
 template <class F, int W, bool PRUNE, bool WIN>
 __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ wrapcol, const KParams& kp,
                           unsigned long long& cells, bool& abandoned) {
@@ -92,6 +98,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     typename F::Col cc[W];
     float v[W], cy[W], wr[W];
     float dg = EAP_FINF, sp = 0.f, s_next = 0.f, fd = 0.f;
+    float4 pk_next = make_float4(0.f, 0.f, 0.f, 0.f);   // packed row constants, one row ahead (F::kPacked)
     bool lane_out = false;
 
     auto left_in = [&](int row) -> float {   // lane 0's left input at `row` of panel p
@@ -141,6 +148,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                 (void)cf;
                 sp = s_before;
                 s_next = __ldg(in.A + r0 - 1);
+                if constexpr (kCtaPacked<F>) pk_next = __ldg(in.rp + r0 - 1);
                 lane_out = c0 > Lb;
             }
             const bool is_last = p == npan - 1;
@@ -152,12 +160,18 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                     float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1);
                     if (lane == 0) x = act ? left_in(row) : EAP_FINF;
                     if (act) {
-                        const float s = s_next;
-                        s_next = __ldg(in.A + min(row, La - 1));
-                        const typename F::Row rc = F::row(s, sp, kp, in.wt);
+                        typename F::Row rc;
+                        if constexpr (kCtaPacked<F>) {
+                            rc = F::unpack(pk_next);
+                            pk_next = __ldg(in.rp + row);   // row <= La: the entry past La is readable
+                        } else {
+                            const float s = s_next;
+                            s_next = __ldg(in.A + min(row, La - 1));
+                            rc = F::row(s, sp, kp, in.wt);
+                            sp = s;
+                        }
                         shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
                         strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
-                        sp = s;
                         dg = x;
                         if (lane == 31) put_out(row, v[W - 1]);
                         if (is_last && lane == res_lane && row == La) {
@@ -297,6 +311,7 @@ __global__ void __launch_bounds__(kCtaThreads) cta_dp_kernel(const DPJob job, co
         in.bB = job.B.border ? job.B.border + ob : nullptr;
         in.wt = job.wdtw_table ? job.wdtw_table + kWdtwOff - max(in.La, in.Lb) : nullptr;
         in.cut_src = cut_src;
+        in.rp = job.rowpack ? job.rowpack + oa : nullptr;
         in.w = pair_window(kp, in.La, in.Lb);
         in.cut = cut;
         bool ab = false;

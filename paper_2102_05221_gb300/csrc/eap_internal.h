@@ -186,14 +186,14 @@ int run_rowpack(const LaunchCtx& c) {
 template <class F, bool WIN>
 int run_kind(const LaunchCtx& c, bool ub_only) {
     if (ub_only) return run_ub<F>(c);
-    if constexpr (!WIN) {
-        if (c.cta) return c.W >= 8 ? run_cta<F, 8>(c) : run_cta<F, 4>(c);
-    }
     LaunchCtx d = c;
     if constexpr (F::kPacked) {
         const int e = run_rowpack<F>(c);
         if (e) return e;
         d.job.rowpack = c.rowpack;
+    }
+    if constexpr (!WIN) {
+        if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     }
     if (c.group && c.prune == eapd::kPmPruned && (c.W == 4 || c.W == 8)) {
         if (c.group == 8) return c.W == 4 ? run_group<F, 4, 8, WIN>(d) : run_group<F, 8, 8, WIN>(d);
