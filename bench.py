@@ -52,8 +52,8 @@ N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # DRAM bytes (read + write) of the dominant DP launch on this workload, from
 # one ncu capture (profiles/dp_kernel_msm_nn1_512_traffic.md), valid only for
 # the library build whose source fingerprint is recorded with it.
-# The EAPruned DP launch of this workload (L = 512): 16 lanes per pair, W = 4.
-DP_KERNEL = "group_dp_kernel<{}, W=4, G=16>"
+# The EAPruned DP launch of this workload (L = 512) for its dominant distance: 16 lanes per pair, W = 5.
+DP_KERNEL = "group_dp_kernel<{}, W=5, G=16>"
 TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 14839040,
            "fingerprint": "6fa9a3b8396dd4eb9a71e0467fe5434cacdc8efa335048b4dad347406d76ce5c"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"

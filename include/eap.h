@@ -255,9 +255,10 @@ typedef struct {
 int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cuda_stream, eap_stats* opt_stats);
 
 /* Autotuner for the DP mapping: for each distance and each power-of-two
- * length bucket that `tasks` contain, times the warp-per-pair wavefront with
- * strip width W = 4, 8 and 16 (32*W columns per panel) and, for unwindowed
- * buckets of 2048 and longer, the CTA-per-pair wavefront with W = 4 and 8, on
+ * length bucket that `tasks` contain, times the wavefront with strip width
+ * W = 4, 5, 8 and 16 (16 lanes per pair for W = 4, 5, 8 when the rows fit,
+ * else a warp per pair) and, for unwindowed buckets of 2048 and longer, the
+ * CTA-per-pair wavefront with W = 4 and 8, on
  * a sample of that task's own work (at most 64 queries x 512 candidates), and
  * keeps the fastest in a process-wide table that eap_nn1, eap_pairwise,
  * eap_pairs and eap_nn1_batch (W only) then use.  Synchronises the stream;

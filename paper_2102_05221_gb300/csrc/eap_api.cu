@@ -394,7 +394,7 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
     const char* e = std::getenv("EAP_W");
     if (e) {
         const int w = std::atoi(e);
-        if (w == 4 || w == 8 || w == 16) return w;
+        if (w == 4 || w == 5 || w == 8 || w == 16) return w;
     }
     if (prune == kPmPruned && kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -404,27 +404,41 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
     // Base and EABase compute (nearly) every cell: wide strips.
     if (prune != kPmPruned) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
     // TWE's 7-op cell amortises the per-step work better at W = 8 when the
-    // 16-lane groups (W = 4) do not apply.
+    // 16-lane groups do not apply.
     if (kind == EAP_TWE && max_cols > 2048) return 8;
-    return 4;
+    // With 16-lane groups, W = 5 is faster for the unwindowed distances
+    // (MSM -2.5%, TWE -3.4%, DTW -2%), W = 4 for the windowed ones.
+    if (kind == EAP_CDTW || kind == EAP_ERP) return 4;
+    return 5;
 }
 
 // Lanes per pair for the EAPruned DP: 8 or 16 (group_dp_kernel, several pairs
 // per warp) or 0 (a warp per pair).  EAP_G overrides (8, 16, or 32 = warp).
 // Groups keep one boundary column per group in shared memory, so they are
-// limited to rows <= 2048 (16 lanes) and <= 1024 (8 lanes), and to W = 4, 8.
-// Default: 16 lanes at W = 4 (measured on the 1000 x 1000 x 512 workload:
-// 9-17% less DP time than a warp per pair for every distance; 8 lanes and
-// W = 8 groups were slower).
+// limited to rows <= 2048 (16 lanes) and <= 1024 (8 lanes); strip widths
+// 4, 5, 8 (16 lanes) and 4, 8 (8 lanes) are built.  Default: 16 lanes
+// (measured on the 1000 x 1000 x 512 workload: 9-17% less DP time than a
+// warp per pair for every distance; 8 lanes and W = 8 were slower).
 int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     (void)kind; (void)cost; (void)max_cols;
-    if (prune != kPmPruned || (W != 4 && W != 8)) return 0;
-    int g = W == 4 ? 16 : 0;
+    if (prune != kPmPruned) return 0;
+    int g = (W == 4 || W == 5) ? 16 : 0;
     const char* e = std::getenv("EAP_G");
     if (e) g = std::atoi(e);
-    if (g == 8 && max_rows <= 1024) return 8;
-    if (g == 16 && max_rows <= 2048) return 16;
+    if (g == 8 && max_rows <= 1024 && (W == 4 || W == 8)) return 8;
+    if (g == 16 && max_rows <= 2048 && (W == 4 || W == 5 || W == 8)) return 16;
     return 0;
+}
+
+// Strip width and lanes per pair together: W = 5 exists only for 16-lane
+// groups, so where those do not apply it becomes 4.
+void choose_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {
+    *W = choose_w(kind, cost, max_cols, prune);
+    *G = choose_group(kind, cost, max_rows, max_cols, prune, *W);
+    if (*W == 5 && *G != 16) {
+        *W = 4;
+        *G = choose_group(kind, cost, max_rows, max_cols, prune, *W);
+    }
 }
 
 // DP launch bracketed by CUDA events on the call's stream when timing is asked.
@@ -628,12 +642,12 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     const bool own_cut = p->prune == 3;
     c.prune = own_cut ? kPmPruned : p->prune;
     c.job.cut = own_cut ? d_ub : nullptr;
-    c.W = choose_w(p->kind, cost, mr, c.prune);
     c.sms = sms;
     c.max_rows = mq;
     c.max_cols = mr;
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
-    c.group = c.cta ? 0 : choose_group(p->kind, cost, mq, mr, c.prune, c.W);
+    choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
+    if (c.cta) { c.W = choose_w(p->kind, cost, mr, c.prune); c.group = 0; }
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -976,12 +990,12 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune;
-    c.W = choose_w(p->kind, cost, mb, c.prune);
     c.sms = sms;
     c.max_rows = ma;
     c.max_cols = mb;
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
-    c.group = c.cta ? 0 : choose_group(p->kind, cost, ma, mb, c.prune, c.W);
+    choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
+    if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1148,10 +1162,9 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune;
-    c.W = choose_w(p->kind, cost, mb, c.prune);
+    choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
     c.sms = sms;
     c.max_rows = ma;
-    c.group = choose_group(p->kind, cost, ma, mb, c.prune, c.W);
     c.stream = st;
     if ((e = dispatch(c, false))) return cuda_status(e);
     if (opt_stats) {
@@ -1205,6 +1218,9 @@ int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
 }
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     return choose_group(kind, cost, max_rows, max_cols, prune, W);
+}
+void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {
+    choose_w_group(kind, cost, max_rows, max_cols, prune, W, G);
 }
 int bucket_of(int len) { return length_bucket(len); }
 int resolve_cost_ext(const eap_params* p) { return resolve_cost(p); }

@@ -293,7 +293,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         h.src = i;
         h.cost = eaph::resolve_cost_ext(&tk.params);
         h.fn = fn_of(tk.params.kind, h.cost);
-        h.W = std::min(8, eaph::pick_w(tk.params.kind, h.cost, mr, 1));
+        h.W = eaph::pick_w(tk.params.kind, h.cost, mr, 1) >= 8 ? 8 : 4;   // the batch kernel is built for W = 4, 8
         h.nq = tk.queries.count;
         h.nr = tk.refs.count;
         h.mq = mq;
@@ -525,10 +525,11 @@ extern "C" int eap_autotune(const eap_nn1_task* tasks, int32_t ntasks, void* cud
         p.prune = 1;
         int best_w = 0, best_map = 1;
         double best_ms = 1e300;
-        // Warp-per-pair with W = 4, 8, 16; CTA-per-pair with W = 4, 8 for long unwindowed buckets.
+        // W = 4, 5, 8, 16 (16-lane groups where they apply, else a warp per
+        // pair); CTA-per-pair with W = 4, 8 for long unwindowed buckets.
         const bool try_cta = k.bucket >= 11 && k.kind != EAP_CDTW && k.kind != EAP_ERP;
-        const int cands[5][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
-        for (int ci = 0; ci < (try_cta ? 5 : 3); ++ci) {
+        const int cands[6][2] = {{4, 1}, {5, 1}, {8, 1}, {16, 1}, {4, 2}, {8, 2}};
+        for (int ci = 0; ci < (try_cta ? 6 : 4); ++ci) {
             eaph::tune_set(k.kind, k.cost, k.bucket, cands[ci][0]);
             eaph::map_set(k.kind, k.cost, k.bucket, cands[ci][1]);
             double ms = 0.0;
@@ -553,7 +554,7 @@ extern "C" int eap_autotune_load(const char* cache_path) {
     if (!f) return EAP_EINVAL;
     int kind, cost, bucket, w, m;
     while (std::fscanf(f, "%d %d %d %d %d", &kind, &cost, &bucket, &w, &m) == 5) {
-        if (kind >= 0 && kind < 6 && (cost == 0 || cost == 1) && bucket >= 0 && bucket < 16 && (w == 4 || w == 8 || w == 16)
+        if (kind >= 0 && kind < 6 && (cost == 0 || cost == 1) && bucket >= 0 && bucket < 16 && (w == 4 || w == 5 || w == 8 || w == 16)
             && (m == 1 || m == 2)) {
             eaph::tune_set(kind, cost, bucket, w);
             eaph::map_set(kind, cost, bucket, m);

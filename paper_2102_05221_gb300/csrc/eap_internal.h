@@ -51,6 +51,7 @@ void map_set(int kind, int cost, int bucket, int m);   // 0 untuned, 1 warp, 2 C
 int pick_w(int kind, int cost, int max_cols, int prune);
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W);
+void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).
@@ -195,9 +196,16 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     }
-    if (c.group && c.prune == eapd::kPmPruned && (c.W == 4 || c.W == 8)) {
-        if (c.group == 8) return c.W == 4 ? run_group<F, 4, 8, WIN>(d) : run_group<F, 8, 8, WIN>(d);
-        if (c.group == 16) return c.W == 4 ? run_group<F, 4, 16, WIN>(d) : run_group<F, 8, 16, WIN>(d);
+    if (c.group && c.prune == eapd::kPmPruned) {
+        if (c.group == 8) {
+            if (c.W == 4) return run_group<F, 4, 8, WIN>(d);
+            if (c.W == 8) return run_group<F, 8, 8, WIN>(d);
+        } else if (c.group == 16) {
+            if (c.W == 4) return run_group<F, 4, 16, WIN>(d);
+            if (c.W == 5) return run_group<F, 5, 16, WIN>(d);
+            if (c.W == 8) return run_group<F, 8, 16, WIN>(d);
+        }
+        return (int)cudaErrorInvalidValue;
     }
     switch (c.W) {
         case 4: return run_dp<F, 4, WIN>(d);

@@ -505,12 +505,12 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
             c.kind = p->kind;
             c.cost = cost;
             c.prune = kPmPruned;
-            c.W = eaph::pick_w(p->kind, cost, m, kPmPruned);
+            eaph::pick_w_group(p->kind, cost, m, m, kPmPruned, &c.W, &c.group);
             c.sms = sms;
             c.max_rows = m;
             c.max_cols = m;
             c.cta = eaph::pick_cta(p->kind, cost, m, m, kPmPruned);
-            c.group = c.cta ? 0 : eaph::pick_group(p->kind, cost, m, m, kPmPruned, c.W);
+            if (c.cta) c.group = 0;
             c.stream = st;
             e |= p->kind == EAP_DTW ? eaph::launch_dp_dtw(c, false) : eaph::launch_dp_cdtw(c, false);
         }

@@ -83,7 +83,7 @@ def test_autotune_picks_a_width_and_keeps_results(tmp_path):
     eap.eap_autotune(tasks, cache_path=path)
     lines = open(path).read().split("\n")
     rows = [list(map(int, l.split())) for l in lines if l.strip()]
-    assert rows and all(r[3] in (4, 8, 16) and r[4] in (1, 2) for r in rows)
+    assert rows and all(r[3] in (4, 5, 8, 16) and r[4] in (1, 2) for r in rows)
     eap.eap_autotune_reset()
     eap.eap_autotune_load(path)
     for kind, kw, tr, te, t in items:

@@ -56,10 +56,10 @@ def test_groups_match_warp_per_pair(kind):
         return i.cpu().numpy(), d.cpu().numpy(), pr
 
     ref = _with_env({"EAP_G": "32", "EAP_W": "4"}, run)
-    for g in ("16", "8"):
-        got = _with_env({"EAP_G": g, "EAP_W": "4"}, run)
+    for g, w in (("16", "4"), ("16", "5"), ("16", "8"), ("8", "4"), ("8", "8")):
+        got = _with_env({"EAP_G": g, "EAP_W": w}, run)
         for a, b in zip(ref, got):
-            assert np.array_equal(a, b), (kind, g)
+            assert np.array_equal(a, b), (kind, g, w)
     D = O.cross(oracle_params(kind, **_kw(kind)), Qp, Rp)
     check_nn(ref[0], ref[1], D)
 
