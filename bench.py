@@ -50,12 +50,12 @@ OPS_PER_CELL = {"dtw": 3, "cdtw": 3, "wdtw": 4, "erp": 5, "msm": 9, "twe": 7}
 LAUNCHES = {"dtw": 5, "cdtw": 5, "wdtw": 6, "erp": 8, "msm": 6, "twe": 6}
 N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # DRAM bytes (read + write) of the dominant DP launch on this workload, from
-# one ncu capture (profiles/dp_kernel_msm_nn1_512_traffic.md), valid only for
+# one ncu capture (profiles/group_dp_kernel_msm_nn1_512_traffic.md), valid only for
 # the library build whose source fingerprint is recorded with it.
 # The EAPruned DP launch of this workload (L = 512) for its dominant distance: 16 lanes per pair, W = 5.
 DP_KERNEL = "group_dp_kernel<{}, W=5, G=16>"
-TRAFFIC = {"kernel": "dp_kernel<msm>", "bytes": 14839040,
-           "fingerprint": "6fa9a3b8396dd4eb9a71e0467fe5434cacdc8efa335048b4dad347406d76ce5c"}
+TRAFFIC = {"kernel": "group_dp_kernel<msm, W=5, G=16>", "bytes": 15071488,
+           "fingerprint": "4e2cc639eb186fb7641e34085be8b3d409dcf672daca255ba5b00ed3e6f7a759"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
