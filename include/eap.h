@@ -153,7 +153,9 @@ int eap_nn1_host(const eap_params* p,
 
 /* All-pairs distance matrix of one set: out_matrix is device float
  * [count * count], row-major, symmetric, zero diagonal.  Each unordered pair
- * is computed once (D(set_i, set_j) with i < j, set_i on the rows). */
+ * is computed once (D(set_i, set_j) with i < j, set_i on the rows).  `mode`
+ * decides the computation (p->prune is not used): EAP_PRUNE_ONLY or
+ * EAP_BASE; both give the same matrix bit for bit. */
 int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matrix, int32_t mode,
                  void* cuda_stream, eap_stats* opt_stats);
 
@@ -161,7 +163,8 @@ int eap_pairwise(const eap_params* p, const eap_series_set* set, float* out_matr
  * if it is <= cutoff[k], else +inf (Section 2.2: an early-abandoned
  * distance signals abandoning by returning +inf).  ia, ib, cutoff, out are
  * device arrays of n elements.  With p->prune = 0 the cut-off is ignored and
- * the plain D is returned. */
+ * the plain D is returned; with p->prune = 2 (EABase) out[k] is D, or +inf
+ * only if D > cutoff[k]; p->prune = 3 is rejected (EAP_EINVAL). */
 int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
               const int32_t* ia, const int32_t* ib, const float* cutoff, float* out, int32_t n,
               void* cuda_stream, eap_stats* opt_stats);
