@@ -7,14 +7,14 @@
 //   2. subseq_query_kernel: the normalised query and its envelope;
 //      envelope_blocks_kernel / envelope_combine_kernel: the running max/min
 //      of the series over +-w in O(n);
-//   3. subseq_bounds_kernel: for every window, in one pass over a shared-
-//      memory tile of the series, the squared Euclidean distance of the
-//      normalised window (the diagonal path: an upper bound of D) and
-//      LB_Keogh both ways (query envelope vs window; the series' envelope,
-//      normalised with the window's mean and deviation, vs query);
-//   4. seed the best-so-far with the smallest upper bound (inflated by its
-//      rounding bound), and compact, in position order, the windows whose
-//      lower bound does not exceed it;
+//   3. subseq_ub_kernel: over shared-memory tiles of the series, the squared
+//      Euclidean distance of each normalised window (its diagonal path: an
+//      upper bound of D), abandoned once above the smallest found so far;
+//      the smallest, inflated by its rounding bound, seeds the best-so-far;
+//   4. subseq_lb_kernel: LB_Keogh both ways (query envelope vs window; the
+//      series' envelope, normalised with the window's mean and deviation,
+//      vs query), abandoned once above the seed, and the order-preserving
+//      compaction of the windows whose bound does not exceed it;
 //   5. chunks of survivors are normalised into scratch and run through the
 //      1-NN DP kernel (EAPruned, one query, shared best-so-far, the lower
 //      bound as Alg. 2's filter before each pair).
@@ -60,11 +60,14 @@ __global__ void subseq_norm_kernel(const float* __restrict__ T, long long npos, 
         s1 += x;
         s2 += x * x;
     }
+    const double inv_m = 1.0 / m;
     for (long long i = i0; i < i1; ++i) {
-        const double mean = s1 / m;
-        const double sd = sqrt(fmax(s2 / m - mean * mean, 0.0));
+        // Sums in FP64 (the variance is a difference of large terms); the
+        // scale 1/deviation only needs float accuracy.
+        const double mean = s1 * inv_m;
+        const double var = fmax(fma(-mean, mean, s2 * inv_m), 0.0);
         mu[i] = (float)mean;
-        isd[i] = sd > kFlatSd ? (float)(1.0 / sd) : 0.f;
+        isd[i] = var > kFlatSd * kFlatSd ? __frsqrt_rn((float)var) : 0.f;
         if (i + 1 < i1) {
             const double a = __ldg(T + i), b = __ldg(T + i + m);
             s1 += b - a;
@@ -159,15 +162,65 @@ __global__ void envelope_combine_kernel(long long n, int w, const float* __restr
     }
 }
 
-// Upper bound (squared Euclidean distance of the normalised window, in the
-// order of the diagonal path) and LB_Keogh both ways for every window.
-// Shared memory: the block's tile of T and of its envelope (blockDim + m - 1
-// floats each) and the normalised query with its envelope (m floats each).
-__global__ void __launch_bounds__(kBoundThreads) subseq_bounds_kernel(
+// Shared-memory tile of the series for the windows of one block: the block's
+// kBoundThreads windows start at i0 and span kBoundThreads + m - 1 points.
+__device__ __forceinline__ void load_tile(float* dst, const float* __restrict__ src, long long i0, long long nT,
+                                          int tile) {
+    for (int k = threadIdx.x; k < tile; k += blockDim.x) {
+        const long long g = i0 + k;
+        dst[k] = g < nT ? __ldg(src + g) : 0.f;
+    }
+}
+
+// Upper bound of every window: the squared Euclidean distance of the
+// normalised window (its diagonal path, summed in the order of the path),
+// abandoned as soon as the partial sum exceeds the smallest bound found so
+// far; only the minimum is kept (one atomicMin per improvement).  Shared
+// memory: the block's tile of T and the normalised query.
+__global__ void __launch_bounds__(kBoundThreads) subseq_ub_kernel(
+        const float* __restrict__ T, long long npos, int m, const float* __restrict__ mu,
+        const float* __restrict__ isd, const float* __restrict__ zq, int cost, unsigned* __restrict__ ub_min) {
+    extern __shared__ float sm[];
+    const int tile = kBoundThreads + m - 1;
+    float* sT = sm;
+    float* sq = sT + tile;
+    const long long i0 = (long long)blockIdx.x * kBoundThreads;
+    load_tile(sT, T, i0, npos + m - 1, tile);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) sq[k] = zq[k];
+    __syncthreads();
+    const long long i = i0 + threadIdx.x;
+    if (i >= npos) return;
+    const float mi = mu[i], si = isd[i];
+    // The running minimum as bits: sums are >= 0, whose floats order as their
+    // bit patterns, and the initial all-ones pattern is above every one.
+    unsigned best = *(volatile const unsigned*)ub_min;
+    float acc = 0.f;
+    int k = 0;
+    for (; k + 32 <= m; k += 32) {
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) acc = __fadd_rn(acc, cost_rt(sq[k + u], znorm1(sT[threadIdx.x + k + u], mi, si), cost));
+        if (__float_as_uint(acc) > best) {
+            best = *(volatile const unsigned*)ub_min;
+            if (__float_as_uint(acc) > best) return;   // this window cannot hold the minimum
+        }
+    }
+    for (; k < m; ++k) acc = __fadd_rn(acc, cost_rt(sq[k], znorm1(sT[threadIdx.x + k], mi, si), cost));
+    if (__float_as_uint(acc) < best) atomicMin(ub_min, __float_as_uint(acc));
+}
+
+// LB_Keogh both ways for every window (query envelope vs window; the series'
+// envelope, normalised like the window, vs query), shrunk by the rounding of
+// the sums so the bound stays below the DP's float D.  A window is abandoned
+// as soon as its partial bound exceeds the cut-off thr: the partial sum is
+// itself a lower bound, larger than thr, which is all the compaction and the
+// DP's filter need.  (Both bounds in one pass: the larger of the two crosses
+// the cut-off sooner than either alone.)  Shared memory: tiles of T and of
+// its envelope, the query's envelope.
+__global__ void __launch_bounds__(kBoundThreads) subseq_lb_kernel(
         const float* __restrict__ T, const float* __restrict__ UT, const float* __restrict__ LT,
         long long npos, int m, const float* __restrict__ mu, const float* __restrict__ isd,
         const float* __restrict__ zq, const float* __restrict__ Uq, const float* __restrict__ Lq, int cost,
-        float* __restrict__ lb, unsigned* __restrict__ ub_min) {
+        const float* __restrict__ thr_p, float* __restrict__ lb) {
     extern __shared__ float sm[];
     const int tile = kBoundThreads + m - 1;
     float* sT = sm;
@@ -178,12 +231,9 @@ __global__ void __launch_bounds__(kBoundThreads) subseq_bounds_kernel(
     float* sqL = sqU + m;
     const long long i0 = (long long)blockIdx.x * kBoundThreads;
     const long long nT = npos + m - 1;
-    for (int k = threadIdx.x; k < tile; k += blockDim.x) {
-        const long long g = i0 + k;
-        sT[k] = g < nT ? __ldg(T + g) : 0.f;
-        sU[k] = g < nT ? __ldg(UT + g) : 0.f;
-        sL[k] = g < nT ? __ldg(LT + g) : 0.f;
-    }
+    load_tile(sT, T, i0, nT, tile);
+    load_tile(sU, UT, i0, nT, tile);
+    load_tile(sL, LT, i0, nT, tile);
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         sq[k] = zq[k];
         sqU[k] = Uq[k];
@@ -191,38 +241,29 @@ __global__ void __launch_bounds__(kBoundThreads) subseq_bounds_kernel(
     }
     __syncthreads();
     const long long i = i0 + threadIdx.x;
-    float ub = EAP_FINF;
-    if (i < npos) {
-        const float mi = mu[i], si = isd[i];
-        float acc = 0.f, lq = 0.f, lc = 0.f;
-        for (int k = 0; k < m; ++k) {
-            const float z = znorm1(sT[threadIdx.x + k], mi, si);
-            const float qk = sq[k];
-            acc = __fadd_rn(acc, cost_rt(qk, z, cost));
-            // Query envelope vs window.
-            const float ex = z > sqU[k] ? cost_rt(z, sqU[k], cost) : (z < sqL[k] ? cost_rt(z, sqL[k], cost) : 0.f);
-            lq = __fadd_rn(lq, ex);
-            // The series' envelope (normalised like the window) vs query.
-            const float uz = znorm1(sU[threadIdx.x + k], mi, si), lz = znorm1(sL[threadIdx.x + k], mi, si);
-            const float ec = qk > uz ? cost_rt(qk, uz, cost) : (qk < lz ? cost_rt(qk, lz, cost) : 0.f);
-            lc = __fadd_rn(lc, ec);
-        }
-        ub = acc;
-        // Shrunk by the rounding of the sums, so the bound stays below the DP's float D.
-        const float shrink = 1.f - (float)(4 * m + 16) * 5.9604645e-8f;
-        lb[i] = fmaxf(lq, lc) * shrink;
+    if (i >= npos) return;
+    const float mi = mu[i], si = isd[i];
+    const float shrink = 1.f - (float)(4 * m + 16) * 5.9604645e-8f;
+    const float thr = *thr_p;
+    float lq = 0.f, lc = 0.f;
+    auto point = [&](int k) {
+        const float z = znorm1(sT[threadIdx.x + k], mi, si);
+        const float qk = sq[k];
+        const float ex = z > sqU[k] ? cost_rt(z, sqU[k], cost) : (z < sqL[k] ? cost_rt(z, sqL[k], cost) : 0.f);
+        lq = __fadd_rn(lq, ex);
+        const float uz = znorm1(sU[threadIdx.x + k], mi, si), lz = znorm1(sL[threadIdx.x + k], mi, si);
+        const float ec = qk > uz ? cost_rt(qk, uz, cost) : (qk < lz ? cost_rt(qk, lz, cost) : 0.f);
+        lc = __fadd_rn(lc, ec);
+    };
+    int k = 0;
+    for (; k + 32 <= m; k += 32) {
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) point(k + u);
+        const float part = fmaxf(lq, lc) * shrink;
+        if (part > thr) { lb[i] = part; return; }
     }
-    // Block minimum of the upper bounds, then one atomic (non-negative floats order as their bits).
-    unsigned bits = __float_as_uint(ub);
-    for (int o = 16; o > 0; o >>= 1) bits = min(bits, __shfl_xor_sync(EAP_FULL, bits, o));
-    __shared__ unsigned wmin[kBoundThreads / 32];
-    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = bits;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned b = wmin[0];
-        for (int k = 1; k < kBoundThreads / 32; ++k) b = min(b, wmin[k]);
-        atomicMin(ub_min, b);
-    }
+    for (; k < m; ++k) point(k);
+    lb[i] = fmaxf(lq, lc) * shrink;
 }
 
 // Cut-off seed: the smallest upper bound, inflated by the rounding bound of
@@ -456,15 +497,20 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
             envelope_combine_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, (long long)sms * 32), 256, 0, st>>>(
                 n, wenv, F(o_gU), F(o_gL), F(o_hU), F(o_hL), F(o_UT), F(o_LT));
         }
-        e |= (int)cudaMemsetAsync(base + o_umin, 0xff, sizeof(unsigned), st);
-        const size_t smem = sizeof(float) * (3 * (size_t)(kBoundThreads + m - 1) + 3 * (size_t)m);
-        if (smem > 48 * 1024)
-            e |= (int)cudaFuncSetAttribute(subseq_bounds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        subseq_bounds_kernel<<<(unsigned)((npos + kBoundThreads - 1) / kBoundThreads), kBoundThreads, smem, st>>>(
-            ref, F(o_UT), F(o_LT), npos, m, F(o_mu), F(o_isd), F(o_zq), F(o_Uq), F(o_Lq), cost, F(o_lb),
-            (unsigned*)(base + o_umin));
+        e |= (int)cudaMemsetAsync(base + o_umin, 0xff, sizeof(unsigned), st);   // all ones: above every sum's bits
+        const unsigned gridb = (unsigned)((npos + kBoundThreads - 1) / kBoundThreads);
+        const size_t smem_ub = sizeof(float) * ((size_t)(kBoundThreads + m - 1) + (size_t)m);
+        if (smem_ub > 48 * 1024)
+            e |= (int)cudaFuncSetAttribute(subseq_ub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_ub);
+        subseq_ub_kernel<<<gridb, kBoundThreads, smem_ub, st>>>(ref, npos, m, F(o_mu), F(o_isd), F(o_zq), cost,
+                                                                (unsigned*)(base + o_umin));
         subseq_seed_kernel<<<1, 1, 0, st>>>((const unsigned*)(base + o_umin), m, F(o_thr),
                                              (unsigned long long*)(base + o_best));
+        const size_t smem_lb = sizeof(float) * (3 * (size_t)(kBoundThreads + m - 1) + 3 * (size_t)m);
+        if (smem_lb > 48 * 1024)
+            e |= (int)cudaFuncSetAttribute(subseq_lb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lb);
+        subseq_lb_kernel<<<gridb, kBoundThreads, smem_lb, st>>>(ref, F(o_UT), F(o_LT), npos, m, F(o_mu), F(o_isd),
+                                                                F(o_zq), F(o_Uq), F(o_Lq), cost, F(o_thr), F(o_lb));
         const int nb = (int)((npos + kCompactBlock - 1) / kCompactBlock);
         compact_count_kernel<<<nb, 256, 0, st>>>(F(o_lb), npos, F(o_thr), (int*)(base + o_cnt));
         compact_scan_kernel<<<1, 1024, 0, st>>>((int*)(base + o_cnt), nb, (int*)(base + o_total));
