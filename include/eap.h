@@ -216,7 +216,9 @@ int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_se
  * LB_Keogh directions are always used).  znorm subtracts the window's mean
  * and divides by its population standard deviation; a deviation of at most
  * 1e-8 normalises the window to zeros.  Ties keep the lowest position.
- * Per query, on the stream: sliding means and deviations of every window;
+ * Per query, on the stream (window statistics and the series' envelope are
+ * reused by consecutive queries of the same length): sliding means and
+ * deviations of every window;
  * for every window the squared Euclidean distance of the normalised window
  * (its diagonal path: an upper bound of D) and LB_Keogh both ways (query
  * envelope vs window, the series' running envelope normalised like the

@@ -470,6 +470,10 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
     unsigned long long* d_stats = (unsigned long long*)(base + o_stats);
     int e = (int)cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * kStatCount, st);
     unsigned long long h_lbskip = 0, h_pos = 0, h_eff = 0;
+    // Window statistics and the series' envelope depend on the query only
+    // through its length (and the window it implies): reused across
+    // consecutive queries of the same length.
+    int stats_m = -1, stats_w = -1;
     for (int q = 0; q < nq && !e && rc == EAP_OK; ++q) {
         const int m = queries->h_lengths[q];
         const long long npos = n - m + 1;
@@ -487,16 +491,19 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
         }
         const int wenv = (int)std::min<long long>(w, m);
         const float* qd = queries->data + queries->h_offsets[q];
-        subseq_norm_kernel<<<(unsigned)((npos + (long long)kNormRun * 128 - 1) / ((long long)kNormRun * 128)), 128, 0,
-                             st>>>(ref, npos, m, F(o_mu), F(o_isd));
+        if (m != stats_m)
+            subseq_norm_kernel<<<(unsigned)((npos + (long long)kNormRun * 128 - 1) / ((long long)kNormRun * 128)), 128,
+                                 0, st>>>(ref, npos, m, F(o_mu), F(o_isd));
         subseq_query_kernel<<<1, 256, 0, st>>>(qd, m, wenv, F(o_zq), F(o_Uq), F(o_Lq));
-        {
+        if (wenv != stats_w) {
             const long long K = 2LL * wenv + 1, nblk = (n + K - 1) / K;
             envelope_blocks_kernel<<<(unsigned)std::min<long long>((nblk + 127) / 128, (long long)sms * 8), 128, 0, st>>>(
                 ref, n, K, F(o_gU), F(o_gL), F(o_hU), F(o_hL));
             envelope_combine_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, (long long)sms * 32), 256, 0, st>>>(
                 n, wenv, F(o_gU), F(o_gL), F(o_hU), F(o_hL), F(o_UT), F(o_LT));
         }
+        stats_m = m;
+        stats_w = wenv;
         e |= (int)cudaMemsetAsync(base + o_umin, 0xff, sizeof(unsigned), st);   // all ones: above every sum's bits
         const unsigned gridb = (unsigned)((npos + kBoundThreads - 1) / kBoundThreads);
         const size_t smem_ub = sizeof(float) * ((size_t)(kBoundThreads + m - 1) + (size_t)m);

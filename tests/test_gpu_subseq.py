@@ -98,3 +98,16 @@ def test_subseq_full_size_sampled(eap):
         for i in sample:
             d_i = O.subseq(p, T[i:i + m], q)[1]
             assert d_i >= float(dist[k]) * (1 - REL_TOL), (k, i, d_i, dist[k])
+
+
+def test_subseq_batch_equals_single_queries(eap):
+    """Queries of equal length share the window statistics inside one call:
+    the batch gives each query's result alone, bit for bit."""
+    T = synth.long_series(30000, 907)
+    Qp, _ = synth.subseq_queries(T, [64, 64, 100, 64, 100, 33], 908, planted=True, noise=0.3)
+    p = eap.params("cdtw", window_ratio=0.1)
+    pos, dist = [x.cpu().numpy() for x in eap.eap_subseq(p, T, eap.SeriesSet.from_packed(Qp))]
+    for k in range(6):
+        one = eap.SeriesSet.from_packed(synth.pack([Qp.series(k)]))
+        p1, d1 = [x.cpu().numpy() for x in eap.eap_subseq(p, T, one)]
+        assert p1[0] == pos[k] and d1[0] == dist[k], (k, p1, pos[k], d1, dist[k])
