@@ -137,7 +137,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                     v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
                 }
                 const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
-                init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
+                init_weights<F, W, WIN>(wr, in.wt, kp, r0, c0, fd, w);
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     if constexpr (F::kCarry) cy[u] = F::carry_init(s_before, cc[u]);
@@ -170,7 +170,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                             rc = F::row(s, sp, kp, in.wt);
                             sp = s;
                         }
-                        shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
+                        shift_weights<F, W, WIN>(wr, in.wt, kp, row, c0, fd, w);
                         strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                         dg = x;
                         if (lane == 31) put_out(row, v[W - 1]);

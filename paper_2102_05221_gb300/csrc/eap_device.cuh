@@ -314,42 +314,46 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const f
         } else {
             nv = F::cell(dg, top, lf, rc, cc[u], dr - u, __fsub_rn(fdr, (float)u), kp);
         }
-        if (WIN) {
-            if ((unsigned)(dr - u + w) > (unsigned)(2 * w)) nv = EAP_FINF;
-        }
+        if (WIN) nv = __fadd_rn(nv, wr[u]);   // 0 inside the window, +inf outside (see shift_weights)
         dg = top;
         v[u] = nv;
         lf = nv;
     }
 }
 
-// Per-cell diagonal factors of a strip (WDTW weights, TWE penalties) for the
-// next row: wr[u] <- wr[u-1], wr[0] <- the factor of i - j = row - c0.  For
-// TWE, fd holds row - 1 - c0 as a float (an exact integer) and steps by one
-// per row, so the penalty of the new cell needs no integer conversion.
-template <class F, int W>
+// Per-cell diagonal factors of a strip for the next row: wr[u] <- wr[u-1],
+// wr[0] <- the factor of i - j = row - c0.  They are WDTW's weights, TWE's
+// penalties, or for the windowed distances the window itself: 0 for
+// |i - j| <= w and +inf outside, added to each cell (a float add instead of a
+// per-cell integer test; x + 0 = x exactly, x + inf = inf).  For TWE, fd
+// holds row - 1 - c0 as a float (an exact integer) and steps by one per row,
+// so the penalty of the new cell needs no integer conversion.
+template <class F, int W, bool WIN>
 __device__ __forceinline__ void shift_weights(float (&wr)[W], const float* wt, const KParams& kp, int row, int c0,
-                                              float& fd) {
-    if constexpr (F::kWeights || F::kPen) {
+                                              float& fd, int w) {
+    if constexpr (F::kWeights || F::kPen || WIN) {
 #pragma unroll
         for (int u = W - 1; u > 0; --u) wr[u] = wr[u - 1];
         if constexpr (F::kWeights) {
             wr[0] = __ldg(wt + 2 * abs(row - c0));
-        } else {
+        } else if constexpr (F::kPen) {
             fd = __fadd_rn(fd, 1.f);
             wr[0] = F::pen_f(kp, fd);
+        } else {
+            wr[0] = abs(row - c0) <= w ? 0.f : EAP_FINF;
         }
     }
 }
 // Factors before a strip's first row r0: those of i - j = r0 - 1 - (c0 + u).
-template <class F, int W>
+template <class F, int W, bool WIN>
 __device__ __forceinline__ void init_weights(float (&wr)[W], const float* wt, const KParams& kp, int r0, int c0,
-                                             float& fd) {
+                                             float& fd, int w) {
     fd = (float)(r0 - 1 - c0);
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         if constexpr (F::kWeights) wr[u] = __ldg(wt + 2 * abs(r0 - 1 - c0 - u));
         else if constexpr (F::kPen) wr[u] = F::pen(kp, r0 - 1 - c0 - u);
+        else if constexpr (WIN) wr[u] = abs(r0 - 1 - c0 - u) <= w ? 0.f : EAP_FINF;
         else wr[u] = 0.f;
     }
 }
@@ -447,7 +451,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
         }
         float wr[W];   // diagonal factors of the strip's cells for the current row (WDTW, TWE)
         float fd;      // row - 1 - c0 as a float (TWE)
-        init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
+        init_weights<F, W, WIN>(wr, in.wt, kp, r0, c0, fd, w);
         float cy[W];   // carried per-cell values of the previous row (TWE)
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
@@ -496,7 +500,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
                     rc = F::row(s, sp, kp, in.wt);
                     sp = s;
                 }
-                shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
+                shift_weights<F, W, WIN>(wr, in.wt, kp, row, c0, fd, w);
                 strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                 dg = x;
                 if (st31) {

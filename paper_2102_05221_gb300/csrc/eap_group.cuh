@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
             cc[u] = F::col(tv, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
-        init_weights<F, W>(wr, in.wt, kp, r0, c0, fd);
+        init_weights<F, W, WIN>(wr, in.wt, kp, r0, c0, fd, in.w);
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
 #pragma unroll
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
                 rc = F::row(s, sp, kp, in.wt);
                 sp = s;
             }
-            shift_weights<F, W>(wr, in.wt, kp, row, c0, fd);
+            shift_weights<F, W, WIN>(wr, in.wt, kp, row, c0, fd, in.w);
             strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, in.w, kp);
             dg = x;
             if (stG) bnd[row] = v[W - 1];
