@@ -401,7 +401,12 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
         const int t = g_tune[kind][cost][length_bucket(max_cols)];
         if (t) return t;
     }
-    // Base and EABase compute (nearly) every cell: wide strips.
+    // Base and EABase compute (nearly) every cell: wide strips, except for the
+    // windowed distances, whose Base DP runs in 8-lane groups (a narrow
+    // staircase wastes fewer cells outside the band |i - j| <= w; measured on
+    // 1000 x 1000 x 512: CDTW W = 8, ERP W = 4 fastest).
+    if (prune == kPmBase && kind == EAP_CDTW) return 8;
+    if (prune == kPmBase && kind == EAP_ERP) return 4;
     if (prune != kPmPruned) return max_cols > 256 ? 16 : (max_cols > 128 ? 8 : 4);
     // TWE's 7-op cell amortises the per-step work better at W = 8 when the
     // 16-lane groups do not apply.
@@ -420,9 +425,11 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
 // (measured on the 1000 x 1000 x 512 workload: 9-17% less DP time than a
 // warp per pair for every distance; 8 lanes and W = 8 were slower).
 int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
-    (void)kind; (void)cost; (void)max_cols;
-    if (prune != kPmPruned) return 0;
-    int g = (W == 4 || W == 5) ? 16 : 0;
+    (void)cost; (void)max_cols;
+    const bool windowed = kind == EAP_CDTW || kind == EAP_ERP;
+    const bool base_windowed = prune == kPmBase && windowed;
+    if (prune != kPmPruned && !base_windowed) return 0;
+    int g = base_windowed ? (max_rows <= 1024 ? 8 : 16) : ((W == 4 || W == 5) ? 16 : 0);
     const char* e = std::getenv("EAP_G");
     if (e) g = std::atoi(e);
     if (g == 8 && max_rows <= 1024 && (W == 4 || W == 8)) return 8;

@@ -16,7 +16,9 @@
 // wavefront steps in lock-step, every lane predicated by its own group's
 // state, (3) one ballot gives each group its frontier vote, and groups whose
 // panel ended process its end (divergent).  The arithmetic of a cell, the
-// pruning rules and the results are those of warp_pair in the EAPruned mode.
+// pruning rules and the results are those of warp_pair in the EAPruned mode
+// (with DPJob::no_cut, of the Base mode: the cut-off is +inf, so every panel
+// runs to its last row and nothing is abandoned).
 #pragma once
 
 #include "eap_device.cuh"
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, con
             bi = __ldg(job.ib + item);
             if (job.cut) c = __ldg(job.cut + item);
         }
+        if (job.no_cut) { c = EAP_FINF; cut_src = nullptr; }   // Base: nothing is pruned or abandoned
         const int64_t oa = __ldg(job.A.off + ai), ob = __ldg(job.B.off + bi);
         in.A = job.A.data + oa;
         in.B = job.B.data + ob;

@@ -196,7 +196,8 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     }
-    if (c.group && c.prune == eapd::kPmPruned) {
+    if (c.group && (c.prune == eapd::kPmPruned || c.prune == eapd::kPmBase)) {
+        d.job.no_cut = c.prune == eapd::kPmBase ? 1 : 0;
         if (c.group == 8) {
             if (c.W == 4) return run_group<F, 4, 8, WIN>(d);
             if (c.W == 8) return run_group<F, 8, 8, WIN>(d);

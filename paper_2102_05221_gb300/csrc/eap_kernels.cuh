@@ -42,7 +42,8 @@ struct DPJob {
     const float* wdtw_table;           // universal WDTW weight table (or null)
     const float* lb;                   // optional per-item lower bound (nn1: [A.n x B.n] by candidate), or null
     const float4* rowpack;             // packed row constants of A (F::kPacked), laid out like A.data, or null
-    int bnd_stride;                    // floats of shared memory per warp
+    int bnd_stride;                    // floats of shared memory per warp (per group for group_dp_kernel)
+    int no_cut;                        // group_dp_kernel: run the Base DP (no cut-off, every cell)
     int pad_;
 };
 
