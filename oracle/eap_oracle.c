@@ -31,7 +31,7 @@
  *                  4.2): windowed min/max envelope, then the sum of the costs
  *                  to the envelope outside it.
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *   - cost(a,b) is squared for DTW/CDTW/WDTW (pinned by DTW(S,T)=9 in the
  *     Fig. DTW caption), absolute for ERP and TWE (their metric forms); MSM
  *     uses |.| as printed.  Either cost can be chosen explicitly.
