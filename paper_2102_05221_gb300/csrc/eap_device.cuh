@@ -81,6 +81,21 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return d;
 }
 
+#ifndef EAP_X2
+#define EAP_X2 1
+#endif
+// Two-cell FP32 arithmetic (add/sub/fma .f32x2 of the sm_100 family): one
+// instruction applies the same operation, with the same rounding, to two
+// neighbouring cells of a strip, halving the issue slots of the cost terms
+// that do not depend on the cell to the left.
+__device__ __forceinline__ float2 sub2_rn(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
 template <int COST>
 __device__ __forceinline__ float pcost(float a, float b) {
     const float d = __fsub_rn(a, b);
@@ -114,6 +129,7 @@ struct FDtw {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;   // the row constant is s_i itself
+    static constexpr bool kX2 = false;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -137,6 +153,7 @@ struct FWdtw {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;
+    static constexpr bool kX2 = false;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -160,19 +177,47 @@ struct FErp {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = true;
     static constexpr bool kPacked = true;    // row constants precomputed per point (rowpack_kernel)
+    static constexpr bool kX2 = EAP_X2;
     struct Col { float t, ct; };
-    struct Row { float s, cs; };
-    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.cs, 0.f, 0.f); }
-    __device__ static Row unpack(const float4& p) { return {p.x, p.y}; }
+    struct Row { float2 s2, cs2; };          // (s_i, s_i), (cost(s_i, g), cost(s_i, g))
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.cs2.x, r.cs2.y); }
+    __device__ static Row unpack(const float4& p) { return {make_float2(p.x, p.y), make_float2(p.z, p.w)}; }
     __device__ static Col col(float t, float, const KParams& kp) { return {t, pcost<COST>(t, kp.erp_gap)}; }
     __device__ static Row row(float s, float, const KParams& kp, const float*) {
-        return {s, pcost<COST>(s, kp.erp_gap)};
+        const float cs = pcost<COST>(s, kp.erp_gap);
+        return {make_float2(s, s), make_float2(cs, cs)};
     }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams&) {
-        const float d = __fsub_rn(r.s, c.t);
+        const float d = __fsub_rn(r.s2.x, c.t);
         const float a = COST == 0 ? __fmaf_rn(d, d, dg) : __fadd_rn(dg, fabsf(d));
-        return min3f(a, __fadd_rn(tp, r.cs), __fadd_rn(lf, c.ct));
+        return min3f(a, __fadd_rn(tp, r.cs2.x), __fadd_rn(lf, c.ct));
+    }
+    // One row of a strip, cell() for every cell with the same operations;
+    // s_i - t_j and the vertical candidate run on neighbouring cells in pairs.
+    template <int W, bool WIN>
+    __device__ static void strip(float (&v)[W], const float (&wr)[W], const Col (&cc)[W], const Row& rc, float dg,
+                                 float lf, const KParams&) {
+        auto diag = [](float d, float g) { return COST == 0 ? __fmaf_rn(d, d, g) : __fadd_rn(g, fabsf(d)); };
+        auto finish = [&](int u, float a, float b) {
+            float nv = min3f(a, b, __fadd_rn(lf, cc[u].ct));
+            if (WIN) nv = __fadd_rn(nv, wr[u]);
+            v[u] = nv;
+            lf = nv;
+        };
+#pragma unroll
+        for (int u = 0; u + 1 < W; u += 2) {
+            const float2 d2 = sub2_rn(rc.s2, make_float2(cc[u].t, cc[u + 1].t));
+            const float2 b2 = __fadd2_rn(make_float2(v[u], v[u + 1]), rc.cs2);
+            const float a0 = diag(d2.x, dg), a1 = diag(d2.y, v[u]);
+            dg = v[u + 1];
+            finish(u, a0, b2.x);
+            finish(u + 1, a1, b2.y);
+        }
+        if constexpr (W % 2 == 1) {
+            constexpr int u = W - 1;
+            finish(u, diag(__fsub_rn(rc.s2.x, cc[u].t), dg), __fadd_rn(v[u], rc.cs2.x));
+        }
     }
 };
 
@@ -200,25 +245,65 @@ struct FMsm {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
+    static constexpr bool kX2 = EAP_X2;
     struct Col { float t, ig, ag; };   // g = t_{j-1} - t_j: ig = 1/g (0 if g = 0), ag = |g|
-    struct Row { float s, ie, ae; };   // e = s_{i-1} - s_i: ie = 1/e (0 if e = 0), ae = |e|
-    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.ie, r.ae, 0.f); }
-    __device__ static Row unpack(const float4& p) { return {p.x, p.y, p.z}; }
+    struct Row { float2 s2; float ie, ae; };   // s2 = (s_i, s_i); e = s_{i-1} - s_i: ie = 1/e (0 if e = 0), ae = |e|
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.ie, r.ae); }
+    __device__ static Row unpack(const float4& p) { return {make_float2(p.x, p.y), p.z, p.w}; }
     __device__ static Col col(float t, float tprev, const KParams&) {
         const float g = __fsub_rn(tprev, t);
         return {t, g != 0.f ? __frcp_rn(g) : 0.f, fabsf(g)};
     }
     __device__ static Row row(float s, float sprev, const KParams&, const float*) {
         const float e = __fsub_rn(sprev, s);
-        return {s, e != 0.f ? __frcp_rn(e) : 0.f, fabsf(e)};
+        return {make_float2(s, s), e != 0.f ? __frcp_rn(e) : 0.f, fabsf(e)};
     }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams& kp) {
-        const float f = __fsub_rn(c.t, r.s);                                   // t_j - s_i
+        const float f = __fsub_rn(c.t, r.s2.x);                                // t_j - s_i
         const float a = __fadd_rn(dg, fabsf(f));                               // move |s_i - t_j|
         const float tc = __fmaf_rn(r.ae, mul_sat(r.ie, f), kp.msm_c);          // C(s_i, s_{i-1}, t_j)
         const float lc = __fmaf_rn(c.ag, mul_sat(c.ig, -f), kp.msm_c);  // C(t_j, t_{j-1}, s_i)
         return min3f(a, __fadd_rn(tp, tc), __fadd_rn(lf, lc));
+    }
+    // One row of a strip, cell() for every cell with the same operations:
+    // the terms that do not depend on the cell to the left (t_j - s_i, both
+    // split/merge costs, the vertical candidate) run on neighbouring cells in
+    // pairs, then the left-to-right chain (horizontal candidate and minimum).
+    template <int W, bool WIN>
+    __device__ static void strip(float (&v)[W], const float (&wr)[W], const Col (&cc)[W], const Row& rc, float dg,
+                                 float lf, const KParams& kp) {
+        float a[W], b[W], lc[W];
+        const float2 c2 = make_float2(kp.msm_c, kp.msm_c);
+        const float2 ae2 = make_float2(rc.ae, rc.ae);
+#pragma unroll
+        for (int u = 0; u + 1 < W; u += 2) {
+            const float2 f2 = sub2_rn(make_float2(cc[u].t, cc[u + 1].t), rc.s2);
+            const float2 tc2 = __ffma2_rn(ae2, make_float2(mul_sat(rc.ie, f2.x), mul_sat(rc.ie, f2.y)), c2);
+            const float2 lc2 = __ffma2_rn(make_float2(cc[u].ag, cc[u + 1].ag),
+                                          make_float2(mul_sat(cc[u].ig, -f2.x), mul_sat(cc[u + 1].ig, -f2.y)), c2);
+            const float2 b2 = __fadd2_rn(make_float2(v[u], v[u + 1]), tc2);
+            a[u] = __fadd_rn(u == 0 ? dg : v[u - 1], fabsf(f2.x));
+            a[u + 1] = __fadd_rn(v[u], fabsf(f2.y));
+            b[u] = b2.x;
+            b[u + 1] = b2.y;
+            lc[u] = lc2.x;
+            lc[u + 1] = lc2.y;
+        }
+        if constexpr (W % 2 == 1) {
+            constexpr int u = W - 1;
+            const float f = __fsub_rn(cc[u].t, rc.s2.x);
+            a[u] = __fadd_rn(u == 0 ? dg : v[u - 1], fabsf(f));
+            b[u] = __fadd_rn(v[u], __fmaf_rn(rc.ae, mul_sat(rc.ie, f), kp.msm_c));
+            lc[u] = __fmaf_rn(cc[u].ag, mul_sat(cc[u].ig, -f), kp.msm_c);
+        }
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            float nv = min3f(a[u], b[u], __fadd_rn(lf, lc[u]));
+            if (WIN) nv = __fadd_rn(nv, wr[u]);
+            v[u] = nv;
+            lf = nv;
+        }
     }
 };
 
@@ -235,6 +320,7 @@ struct FTwe {
     static constexpr bool kPen = true;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
+    static constexpr bool kX2 = false;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
     struct Row { float s, sprev, ga; };   // ga = cost(s_i, s_{i-1}) + nu + lambda
     __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sprev, r.ga, 0.f); }
@@ -298,6 +384,10 @@ template <class F, int W, bool WIN>
 __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const float (&wr)[W],
                                           const typename F::Col (&cc)[W], const typename F::Row& rc, float dg,
                                           float lf, int dr, int w, const KParams& kp) {
+    if constexpr (F::kX2) {
+        F::template strip<W, WIN>(v, wr, cc, rc, dg, lf, kp);
+        return;
+    }
     const float fdr = (float)dr;
     float carry_prev = 0.f;
     if constexpr (F::kCarry) carry_prev = F::carry_first(rc, cc[0]);
