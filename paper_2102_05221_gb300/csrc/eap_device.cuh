@@ -84,6 +84,29 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 #ifndef EAP_X2
 #define EAP_X2 1
 #endif
+#ifndef EAP_X2_TWE
+#define EAP_X2_TWE EAP_X2
+#endif
+// Resident blocks per SM that group_dp_kernel asks the register allocator
+// for (strip widths up to 5; 0 leaves the choice to the compiler, which then
+// takes the fewest registers that do not spill).  TWE's paired cells need 103
+// registers, one block fewer per SM; capped at 96 (a 16-byte spill) it runs
+// 9% faster on 1000 x 1000 x 512 (37.2 ms against 40.8).
+#ifndef EAP_MINB_DTW
+#define EAP_MINB_DTW 0
+#endif
+#ifndef EAP_MINB_WDTW
+#define EAP_MINB_WDTW 0
+#endif
+#ifndef EAP_MINB_ERP
+#define EAP_MINB_ERP 0
+#endif
+#ifndef EAP_MINB_MSM
+#define EAP_MINB_MSM 0
+#endif
+#ifndef EAP_MINB_TWE
+#define EAP_MINB_TWE 5
+#endif
 // Two-cell FP32 arithmetic (add/sub/fma .f32x2 of the sm_100 family): one
 // instruction applies the same operation, with the same rounding, to two
 // neighbouring cells of a strip, halving the issue slots of the cost terms
@@ -130,6 +153,7 @@ struct FDtw {
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;   // the row constant is s_i itself
     static constexpr bool kX2 = false;
+    static constexpr int kGroupBlocks = EAP_MINB_DTW;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -154,6 +178,7 @@ struct FWdtw {
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;
     static constexpr bool kX2 = false;
+    static constexpr int kGroupBlocks = EAP_MINB_WDTW;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -178,6 +203,7 @@ struct FErp {
     static constexpr bool kBorders = true;
     static constexpr bool kPacked = true;    // row constants precomputed per point (rowpack_kernel)
     static constexpr bool kX2 = EAP_X2;
+    static constexpr int kGroupBlocks = EAP_MINB_ERP;
     struct Col { float t, ct; };
     struct Row { float2 s2, cs2; };          // (s_i, s_i), (cost(s_i, g), cost(s_i, g))
     __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.cs2.x, r.cs2.y); }
@@ -196,8 +222,8 @@ struct FErp {
     // One row of a strip, cell() for every cell with the same operations;
     // s_i - t_j and the vertical candidate run on neighbouring cells in pairs.
     template <int W, bool WIN>
-    __device__ static void strip(float (&v)[W], const float (&wr)[W], const Col (&cc)[W], const Row& rc, float dg,
-                                 float lf, const KParams&) {
+    __device__ static void strip(float (&v)[W], float (&)[W], const float (&wr)[W], const Col (&cc)[W],
+                                 const Row& rc, float dg, float lf, const KParams&) {
         auto diag = [](float d, float g) { return COST == 0 ? __fmaf_rn(d, d, g) : __fadd_rn(g, fabsf(d)); };
         auto finish = [&](int u, float a, float b) {
             float nv = min3f(a, b, __fadd_rn(lf, cc[u].ct));
@@ -246,6 +272,7 @@ struct FMsm {
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
     static constexpr bool kX2 = EAP_X2;
+    static constexpr int kGroupBlocks = EAP_MINB_MSM;
     struct Col { float t, ig, ag; };   // g = t_{j-1} - t_j: ig = 1/g (0 if g = 0), ag = |g|
     struct Row { float2 s2; float ie, ae; };   // s2 = (s_i, s_i); e = s_{i-1} - s_i: ie = 1/e (0 if e = 0), ae = |e|
     __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.ie, r.ae); }
@@ -271,8 +298,8 @@ struct FMsm {
     // split/merge costs, the vertical candidate) run on neighbouring cells in
     // pairs, then the left-to-right chain (horizontal candidate and minimum).
     template <int W, bool WIN>
-    __device__ static void strip(float (&v)[W], const float (&wr)[W], const Col (&cc)[W], const Row& rc, float dg,
-                                 float lf, const KParams& kp) {
+    __device__ static void strip(float (&v)[W], float (&)[W], const float (&wr)[W], const Col (&cc)[W],
+                                 const Row& rc, float dg, float lf, const KParams& kp) {
         float a[W], b[W], lc[W];
         const float2 c2 = make_float2(kp.msm_c, kp.msm_c);
         const float2 ae2 = make_float2(rc.ae, rc.ae);
@@ -320,16 +347,18 @@ struct FTwe {
     static constexpr bool kPen = true;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = true;
-    static constexpr bool kX2 = false;
+    static constexpr bool kX2 = EAP_X2_TWE;
+    static constexpr int kGroupBlocks = EAP_MINB_TWE;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
-    struct Row { float s, sprev, ga; };   // ga = cost(s_i, s_{i-1}) + nu + lambda
-    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sprev, r.ga, 0.f); }
-    __device__ static Row unpack(const float4& p) { return {p.x, p.y, p.z}; }
+    struct Row { float s, sprev; float2 ga2; };   // ga2 = (ga, ga), ga = cost(s_i, s_{i-1}) + nu + lambda
+    __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sprev, r.ga2.x, r.ga2.y); }
+    __device__ static Row unpack(const float4& p) { return {p.x, p.y, make_float2(p.z, p.w)}; }
     __device__ static Col col(float t, float tprev, const KParams& kp) {
         return {t, tprev, __fadd_rn(__fadd_rn(pcost<COST>(t, tprev), kp.twe_nu), kp.twe_lambda)};
     }
     __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
-        return {s, sprev, __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda)};
+        const float ga = __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda);
+        return {s, sprev, make_float2(ga, ga)};
     }
     // 2 nu |i - j| for a cell with i - j = d (an integer, or its exact float).
     __device__ static float pen(const KParams& kp, int d) { return __fmul_rn(kp.twe_nu2, (float)abs(d)); }
@@ -338,7 +367,7 @@ struct FTwe {
                                  const KParams& kp) {
         const float gm0 = __fadd_rn(pcost<COST>(r.s, c.t), pcost<COST>(r.sprev, c.tprev));
         const float gm = __fadd_rn(gm0, pen(kp, dij));
-        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
+        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga2.x), __fadd_rn(lf, c.gb));
     }
     // The same cell with cost(s_{i-1}, t_{j-1}) given (carry_in), the
     // penalty given (pn = pen(i - j)) and cost(s_i, t_j) returned for the
@@ -348,10 +377,40 @@ struct FTwe {
         const float c1 = pcost<COST>(r.s, c.t);
         carry_out = c1;
         const float gm = __fadd_rn(__fadd_rn(c1, carry_in), pn);
-        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga), __fadd_rn(lf, c.gb));
+        return min3f(__fadd_rn(dg, gm), __fadd_rn(tp, r.ga2.x), __fadd_rn(lf, c.gb));
     }
     __device__ static float carry_first(const Row& r, const Col& c0) { return pcost<COST>(r.sprev, c0.tprev); }
     __device__ static float carry_init(float sprev, const Col& c) { return pcost<COST>(sprev, c.t); }
+    // One row of a strip, cell_c() for every cell with the same operations;
+    // s_i - t_j and the vertical candidate run on neighbouring cells in pairs.
+    template <int W, bool WIN>
+    __device__ static void strip(float (&v)[W], float (&cy)[W], const float (&wr)[W], const Col (&cc)[W],
+                                 const Row& rc, float dg, float lf, const KParams&) {
+        static_assert(!WIN, "TWE has no window");
+        auto pc = [](float d) { return COST == 0 ? __fmul_rn(d, d) : fabsf(d); };
+        float cin = carry_first(rc, cc[0]);
+        auto finish = [&](int u, float dgu, float c1, float b) {
+            const float gm = __fadd_rn(__fadd_rn(c1, cin), wr[u]);
+            cin = cy[u];
+            cy[u] = c1;
+            const float nv = min3f(__fadd_rn(dgu, gm), b, __fadd_rn(lf, cc[u].gb));
+            v[u] = nv;
+            lf = nv;
+        };
+#pragma unroll
+        for (int u = 0; u + 1 < W; u += 2) {
+            const float2 d2 = sub2_rn(make_float2(rc.s, rc.s), make_float2(cc[u].t, cc[u + 1].t));
+            const float2 b2 = __fadd2_rn(make_float2(v[u], v[u + 1]), rc.ga2);
+            const float dg0 = dg, dg1 = v[u];
+            dg = v[u + 1];
+            finish(u, dg0, pc(d2.x), b2.x);
+            finish(u + 1, dg1, pc(d2.y), b2.y);
+        }
+        if constexpr (W % 2 == 1) {
+            constexpr int u = W - 1;
+            finish(u, dg, pc(__fsub_rn(rc.s, cc[u].t)), __fadd_rn(v[u], rc.ga2.x));
+        }
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -385,7 +444,7 @@ __device__ __forceinline__ void strip_row(float (&v)[W], float (&cy)[W], const f
                                           const typename F::Col (&cc)[W], const typename F::Row& rc, float dg,
                                           float lf, int dr, int w, const KParams& kp) {
     if constexpr (F::kX2) {
-        F::template strip<W, WIN>(v, wr, cc, rc, dg, lf, kp);
+        F::template strip<W, WIN>(v, cy, wr, cc, rc, dg, lf, kp);
         return;
     }
     const float fdr = (float)dr;

@@ -36,8 +36,11 @@ __device__ __forceinline__ unsigned group_mask(int lane) {
     return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
+template <class F, int W>
+constexpr int group_min_blocks() { return W <= 5 ? F::kGroupBlocks : 0; }
+
 template <class F, int W, int G, bool WIN>
-__global__ void __launch_bounds__(kThreads) group_dp_kernel(const DPJob job, const KParams kp) {
+__global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp_kernel(const DPJob job, const KParams kp) {
     static_assert(G == 8 || G == 16, "group width");
     constexpr int P = G * W;                 // columns per panel
     constexpr int NG = 32 / G;               // groups per warp
