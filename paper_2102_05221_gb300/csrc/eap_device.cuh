@@ -89,9 +89,9 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 #endif
 // Resident blocks per SM that group_dp_kernel asks the register allocator
 // for (strip widths up to 5; 0 leaves the choice to the compiler, which then
-// takes the fewest registers that do not spill).  TWE's paired cells need 103
-// registers, one block fewer per SM; capped at 96 (a 16-byte spill) it runs
-// 9% faster on 1000 x 1000 x 512 (37.2 ms against 40.8).
+// takes the fewest registers that do not spill).  With the group's cold state
+// in shared memory every distance's default is the fastest measured on
+// 1000 x 1000 x 512 (TWE: 88 registers, 34.8 ms; capped at 80, 35.2 ms).
 #ifndef EAP_MINB_DTW
 #define EAP_MINB_DTW 0
 #endif
@@ -105,7 +105,7 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 #define EAP_MINB_MSM 0
 #endif
 #ifndef EAP_MINB_TWE
-#define EAP_MINB_TWE 5
+#define EAP_MINB_TWE 0
 #endif
 // Two-cell FP32 arithmetic (add/sub/fma .f32x2 of the sm_100 family): one
 // instruction applies the same operation, with the same rounding, to two

@@ -51,23 +51,36 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
     const int gl = lane & (G - 1);           // lane within the group
     const unsigned gmask = group_mask<G>(lane);
     float* bnd = smem + ((threadIdx.x >> 5) * NG + lane / G) * job.bnd_stride;
-    unsigned long long cells = 0, npairs = 0, nab = 0, nlb = 0;
+
+    // Group state that only the set-up and the end of a pair or a panel read
+    // lives in shared memory, so that the registers of the wavefront loop
+    // hold only what a step uses (more resident warps per SM).  Every lane of
+    // the group writes the same values and reads back its own writes; the
+    // counters belong to the group's first lane.
+    struct Cold {
+        PairIn in;
+        unsigned long long item;
+        int ai, bi, npan, p, blo, cf, cl;
+        bool last;
+        unsigned long long npairs, nab, nlb;
+    };
+    __shared__ Cold cold_all[kThreads / G];
+    Cold& gc = cold_all[threadIdx.x / G];
+    if (gl == 0) gc.npairs = gc.nab = gc.nlb = 0;
+    unsigned long long cells = 0;
 
     int state = kNeedPair;
-    // Pair state (uniform within the group).
-    PairIn in;
-    in.A = in.B = in.bA = in.bB = in.wt = nullptr;
-    in.rp = nullptr;
-    in.cut_src = nullptr;
-    in.La = in.Lb = 0;
-    in.w = 0;
-    in.cut = EAP_FINF;
-    unsigned long long item = 0;
-    int ai = 0, bi = 0, npan = 0, p = 0, blo = 1, bhi = 0;
     float cut = EAP_FINF;
+    int bhi = 0;
+    // What a wavefront step reads of the pair.
+    const float4* rp = nullptr;   // packed row constants (F::kPacked)
+    const float* Ar = nullptr;    // row series (rows computed in place)
+    int La = 0;
+    const float* wt = nullptr;    // WDTW weights
+    int w = 0;                    // window
     // Panel state.
-    int cf = 0, cl = 0, r0 = 1, r1 = 0, t = 0, nsteps = 0, c0 = 0, nvalid = 0;
-    bool last = false, lane_out = true, stG = false;
+    int r0 = 1, r1 = 0, t = 0, nsteps = 0, c0 = 0;
+    bool lane_out = true, stG = false;
     typename F::Col cc[W];
     float v[W], wr[W], cy[W];
 #pragma unroll
@@ -78,8 +91,9 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
     // The group leader publishes a pair's result.
     auto finish_pair = [&](float d, bool ab) {
         if (gl == 0) {
-            ++npairs;
-            nab += ab ? 1 : 0;
+            ++gc.npairs;
+            gc.nab += ab ? 1 : 0;
+            const int ai = gc.ai, bi = gc.bi;
             if (job.mode == kModeNN1) {
                 if (d != EAP_FINF) atomicMin(job.best + ai, pack_best(d, (unsigned)bi));
             } else if (job.mode == kModePairwise) {
@@ -87,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
                 job.out[(size_t)ai * n + bi] = d;
                 job.out[(size_t)bi * n + ai] = d;
             } else {
-                job.out[item] = d;
+                job.out[gc.item] = d;
             }
         }
         __syncwarp(gmask);
@@ -99,7 +113,8 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         if (gl == 0) it = atomicAdd(job.counter, 1ULL);
         it = __shfl_sync(gmask, it, 0, G);
         if (it >= job.nitems) { state = kDone; return; }
-        item = it;
+        const unsigned long long item = it;
+        int ai, bi;
         const unsigned long long* cut_src = nullptr;
         float c = EAP_FINF;
         if (job.mode == kModeNN1) {
@@ -115,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
                 cv = __shfl_sync(gmask, cv, 0, G);
                 c = __uint_as_float((unsigned)(cv >> 32));
                 if (job.lb && __ldg(job.lb + (size_t)ai * job.B.n + bi) > c) {   // Alg. 2
-                    if (gl == 0) ++nlb;
+                    if (gl == 0) ++gc.nlb;
                     return;   // still kNeedPair
                 }
             }
@@ -129,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         }
         if (job.no_cut) { c = EAP_FINF; cut_src = nullptr; }   // Base: nothing is pruned or abandoned
         const int64_t oa = __ldg(job.A.off + ai), ob = __ldg(job.B.off + bi);
+        PairIn in;
         in.A = job.A.data + oa;
         in.B = job.B.data + ob;
         in.La = __ldg(job.A.len + ai);
@@ -140,12 +156,21 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         in.cut_src = cut_src;
         in.w = pair_window(kp, in.La, in.Lb);
         in.cut = c;
+        gc.in = in;
+        gc.item = item;
+        gc.ai = ai;
+        gc.bi = bi;
+        gc.p = 0;
+        rp = in.rp;
+        Ar = in.A;
+        La = in.La;
+        wt = in.wt;
+        w = in.w;
         cut = c;
         if (in.w < abs(in.La - in.Lb)) { finish_pair(EAP_FINF, true); return; }   // no alignment in the window
-        npan = (in.Lb + P - 1) / P;
-        p = 0;
+        gc.npan = (in.Lb + P - 1) / P;
         // Left boundary of panel 0: the vertical border M(r, 0) (ERP), else +inf.
-        blo = 1;
+        int blo = 1;
         bhi = 0;
         if (F::kBorders) {
             const int vmax = min(in.La, in.w + 1);
@@ -158,15 +183,21 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             }
             if (live > 0) { blo = 1; bhi = live; }   // the border increases: live rows are a prefix
         }
+        gc.blo = blo;
         __syncwarp(gmask);
         state = kNeedPanel;
     };
 
     auto begin_panel = [&]() {
-        const int La = in.La, Lb = in.Lb, w = in.w;
-        cf = p * P + 1;
-        cl = min(cf + P - 1, Lb);
-        last = (p == npan - 1);
+        const PairIn in = gc.in;
+        const int Lb = in.Lb;
+        const int p = gc.p, blo = gc.blo;
+        const int cf = p * P + 1;
+        const int cl = min(cf + P - 1, Lb);
+        const bool last = (p == gc.npan - 1);
+        gc.cf = cf;
+        gc.cl = cl;
+        gc.last = last;
         if (in.cut_src) {
             unsigned long long cv = 0;
             if (gl == 0) cv = *(volatile const unsigned long long*)in.cut_src;
@@ -180,9 +211,10 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         if (WIN) { r0 = max(r0, cf - w); r1 = min(La, cl + w); }
         if (r0 > r1) {
             if (last) { finish_pair(EAP_FINF, true); return; }
-            blo = 1;
+            __syncwarp(gmask);   // every lane has read p and blo
+            gc.blo = 1;
             bhi = 0;
-            ++p;
+            gc.p = p + 1;
             return;   // still kNeedPanel
         }
         for (int r = r0 + gl; r <= r1; r += G)
@@ -197,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             cc[u] = F::col(tv, tprev, kp);
             v[u] = (r0 == 1) ? hborder<F>(in, c <= Lb ? c : Lb + 1) : EAP_FINF;
         }
-        init_weights<F, W, WIN>(wr, in.wt, kp, r0, c0, fd, in.w);
+        init_weights<F, W, WIN>(wr, wt, kp, r0, c0, fd, w);
         {
             const float s_before = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
 #pragma unroll
@@ -209,13 +241,12 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         if (r0 == 1) dg = hborder<F>(in, c0 - 1 <= Lb ? c0 - 1 : Lb + 1);
         else dg = (gl == 0) ? bnd[r0 - 1] : EAP_FINF;
         lane_out = c0 > Lb;
-        nvalid = max(0, min(W, Lb - c0 + 1));
         stG = !last && gl == G - 1;
         if constexpr (F::kPacked) {
-            pk_next = __ldg(in.rp + r0 - 1);
+            pk_next = __ldg(rp + r0 - 1);
         } else {
-            sp = r0 >= 2 ? __ldg(in.A + r0 - 2) : 0.f;
-            s_next = __ldg(in.A + r0 - 1);
+            sp = r0 >= 2 ? __ldg(Ar + r0 - 2) : 0.f;
+            s_next = __ldg(Ar + r0 - 1);
         }
         nsteps = r1 - r0 + G;
         t = 0;
@@ -224,13 +255,14 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
 
     // End of the current panel after `done` steps.
     auto end_panel = [&](int done) {
-        const int La = in.La, Lb = in.Lb;
+        const int Lb = gc.in.Lb, cf = gc.cf, p = gc.p;
         {
             const int lastrow = min(r1, r0 + done - 1 - gl);
+            const int nvalid = max(0, min(W, Lb - c0 + 1));
             if (lastrow >= r0) cells += (unsigned long long)(lastrow - r0 + 1) * (unsigned)nvalid;
         }
         __syncwarp(gmask);
-        if (last) {
+        if (gc.last) {
             const int off = Lb - cf;         // offset of column Lb inside the panel
             const int lr = off / W, ur = off % W;
             float res = EAP_FINF;
@@ -254,9 +286,9 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             lo = min(lo, __shfl_xor_sync(gmask, lo, o, G));
             hi = max(hi, __shfl_xor_sync(gmask, hi, o, G));
         }
-        if (hi < 0) { blo = 1; bhi = 0; } else { blo = lo; bhi = hi; }
+        if (hi < 0) { gc.blo = 1; bhi = 0; } else { gc.blo = lo; bhi = hi; }
+        gc.p = p + 1;
         __syncwarp(gmask);
-        ++p;
         state = kNeedPanel;
     };
 
@@ -274,15 +306,15 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             typename F::Row rc;
             if constexpr (F::kPacked) {
                 rc = F::unpack(pk_next);
-                pk_next = __ldg(in.rp + row);   // row <= La: the entry past La is readable
+                pk_next = __ldg(rp + row);   // row <= La: the entry past La is readable
             } else {
                 const float s = s_next;
-                s_next = __ldg(in.A + min(row, in.La - 1));
-                rc = F::row(s, sp, kp, in.wt);
+                s_next = __ldg(Ar + min(row, La - 1));
+                rc = F::row(s, sp, kp, wt);
                 sp = s;
             }
-            shift_weights<F, W, WIN>(wr, in.wt, kp, row, c0, fd, in.w);
-            strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, in.w, kp);
+            shift_weights<F, W, WIN>(wr, wt, kp, row, c0, fd, w);
+            strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
             dg = x;
             if (stG) bnd[row] = v[W - 1];
         }
@@ -327,6 +359,8 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         }
     }
     if (job.stats) {
+        unsigned long long npairs = 0, nab = 0, nlb = 0;
+        if (gl == 0) { npairs = gc.npairs; nab = gc.nab; nlb = gc.nlb; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             cells += __shfl_xor_sync(EAP_FULL, cells, o);
