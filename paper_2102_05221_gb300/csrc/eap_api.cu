@@ -438,6 +438,34 @@ int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int 
     return 0;
 }
 
+// Band mapping (band_dp_kernel) for the Base DP of CDTW and ERP: a row of the
+// window, plus the two border cells it reaches, is 2w + 3 cells; the
+// narrowest built launch that holds the widest pair's band is taken, if the
+// band is narrower than the series (else the column-panel kernels do less
+// work).  EAP_BAND=0 turns it off.
+void choose_band(int kind, int prune, const KParams& kp, int max_rows, int max_cols, int* W, int* G) {
+    *W = 0;
+    *G = 0;
+    if (prune != kPmBase || (kind != EAP_CDTW && kind != EAP_ERP)) return;
+    const char* e = std::getenv("EAP_BAND");
+    if (e && std::atoi(e) == 0) return;
+    const int L = max_rows > max_cols ? max_rows : max_cols;
+    long long w;
+    if (kp.window_abs >= 0) w = kp.window_abs;
+    else if (kp.window_ratio >= 0.f) w = (long long)std::floor((double)kp.window_ratio * (double)L);
+    else return;
+    const long long B = 2 * w + 3;
+    if (B > L) return;
+    static const int kBands[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};   // (W, G)
+    for (const auto& b : kBands) {
+        if ((long long)b[0] * b[1] >= B) {
+            *W = b[0];
+            *G = b[1];
+            return;
+        }
+    }
+}
+
 // Strip width and lanes per pair together: W = 5 exists only for 16-lane
 // groups, so where those do not apply it becomes 4.
 void choose_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {
@@ -656,6 +684,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
     choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mr, c.prune); c.group = 0; }
+    choose_band(p->kind, c.prune, c.kp, mq, mr, &c.band, &c.band_g);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -912,6 +941,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.max_cols = mx;
         c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
         c.group = c.cta ? 0 : choose_group(p->kind, cost, mx, mx, c.prune, c.W);
+        choose_band(p->kind, c.prune, c.kp, mx, mx, &c.band, &c.band_g);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -1004,6 +1034,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
+    choose_band(p->kind, c.prune, c.kp, ma, mb, &c.band, &c.band_g);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1171,8 +1202,10 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.cost = cost;
     c.prune = p->prune;
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
+    choose_band(p->kind, c.prune, c.kp, ma, mb, &c.band, &c.band_g);
     c.sms = sms;
     c.max_rows = ma;
+    c.max_cols = mb;
     c.stream = st;
     if ((e = dispatch(c, false))) return cuda_status(e);
     if (opt_stats) {
@@ -1227,6 +1260,10 @@ int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     return choose_group(kind, cost, max_rows, max_cols, prune, W);
 }
+void pick_band(int kind, int prune, const KParams& kp, int max_rows, int max_cols, int* W, int* G) {
+    choose_band(kind, prune, kp, max_rows, max_cols, W, G);
+}
+
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {
     choose_w_group(kind, cost, max_rows, max_cols, prune, W, G);
 }

@@ -24,6 +24,8 @@ struct LaunchCtx {
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
     int cta;             // 1: CTA-per-pair mapping (long, unwindowed series); 0: warp per pair
+    int band = 0;        // Base DP of a windowed distance in band coordinates: strip width (0 = not used)
+    int band_g = 0;      // lanes per pair of the band mapping
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
 };
@@ -52,6 +54,8 @@ int pick_w(int kind, int cost, int max_cols, int prune);
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W);
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G);
+// Band mapping of the windowed Base DP: strip width and lanes per pair, or 0.
+void pick_band(int kind, int prune, const eapd::KParams& kp, int max_rows, int max_cols, int* W, int* G);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).
@@ -100,6 +104,24 @@ int run_dp(const LaunchCtx& c) {
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kThreads, smem, c.stream>>>(c.job, c.kp);
+    return (int)cudaGetLastError();
+}
+
+// Base DP of a windowed distance in band coordinates (band_dp_kernel), G lanes per pair.
+template <class F, int W, int G>
+int run_band(const LaunchCtx& c) {
+    using namespace eapd;
+    void (*kern)(const DPJob, const KParams) = band_dp_kernel<F, W, G>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    unsigned long long grid = (unsigned long long)per_sm * c.sms;
+    const unsigned long long per_block = (unsigned long long)kWarpsPerBlock * (32 / G);
+    const unsigned long long need = (c.job.nitems + per_block - 1) / per_block;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kThreads, 0, c.stream>>>(c.job, c.kp);
     return (int)cudaGetLastError();
 }
 
@@ -195,6 +217,18 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
     }
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
+    } else {
+        if (c.band && c.prune == eapd::kPmBase) {
+            if (c.band_g == 8) {
+                if (c.band == 4) return run_band<F, 4, 8>(d);
+                if (c.band == 8) return run_band<F, 8, 8>(d);
+                if (c.band == 14) return run_band<F, 14, 8>(d);
+                if (c.band == 16) return run_band<F, 16, 8>(d);
+            } else if (c.band_g == 16 && c.band == 16) {
+                return run_band<F, 16, 16>(d);
+            }
+            return (int)cudaErrorInvalidValue;
+        }
     }
     if (c.group && (c.prune == eapd::kPmPruned || c.prune == eapd::kPmBase)) {
         d.job.no_cut = c.prune == eapd::kPmBase ? 1 : 0;

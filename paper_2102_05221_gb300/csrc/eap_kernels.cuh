@@ -241,3 +241,4 @@ __global__ void __launch_bounds__(32 * kUbTileWarps) ub_tile_kernel(const DPJob 
 
 #include "eap_cta.cuh"
 #include "eap_group.cuh"
+#include "eap_band.cuh"

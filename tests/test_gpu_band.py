@@ -1,0 +1,117 @@
+"""Base DP of the windowed distances (CDTW, ERP) in band coordinates
+(band_dp_kernel): bit-identical to the column-panel Base kernels (the band
+mapping switched off with EAP_BAND=0) and within tolerance of the FP64
+oracle, on ragged lengths, windows at and around every built band width,
+the degenerate windows (w = 0, w = |L_A - L_B|) and the three entry points
+that run the Base DP (pairs, 1-NN with prune = 0, all-pairs matrix)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2102_05221_gb300 import synth
+from tests.parity_util import close, check_nn, gpu_params, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+# Band rows hold 2w + 3 cells; the built launches hold 32, 64, 112, 128, 256.
+BAND_WINDOWS = [0, 1, 2, 14, 15, 30, 31, 54, 55, 62, 63, 126, 127]
+
+
+@pytest.fixture(scope="module")
+def eap():
+    from paper_2102_05221_gb300 import eap as E
+    E.load()
+    return E
+
+
+def _run(fn, band):
+    old = os.environ.get("EAP_BAND")
+    if band:
+        os.environ.pop("EAP_BAND", None)
+    else:
+        os.environ["EAP_BAND"] = "0"
+    try:
+        return fn()
+    finally:
+        if old is None:
+            os.environ.pop("EAP_BAND", None)
+        else:
+            os.environ["EAP_BAND"] = old
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+@pytest.mark.parametrize("cost", [0, 1])
+@pytest.mark.parametrize("w", BAND_WINDOWS)
+def test_band_pairs_match_panels_and_oracle(eap, kind, cost, w):
+    rng = np.random.default_rng(7000 + 31 * w + cost + (kind == "erp") * 1000)
+    L = max(2 * w + 3, 40)
+    # Equal lengths, lengths differing by up to w, and a few short series.
+    la = [L, L, L + 1, L + w, max(1, L - w), L + 3 if w >= 3 else L, 2 * w + 3, 1 if w >= 1 else L]
+    lb = [L, L + w, L, L, L, L, 2 * w + 3, 2 if w >= 1 else L]
+    Ap = synth.ragged_walks(len(la), la, 900 + w, n_classes=2)
+    Bp = synth.ragged_walks(len(lb), lb, 901 + w, n_classes=2)
+    A, B = eap.SeriesSet.from_packed(Ap), eap.SeriesSet.from_packed(Bp)
+    kw = {"window": w, "cost": cost}
+    if kind == "erp":
+        kw["erp_gap"] = float(np.float32(rng.uniform(-0.5, 0.5)))
+    p = gpu_params(eap, kind, prune=0, **kw)
+    ia = np.repeat(np.arange(len(la)), len(lb)).astype(np.int32)
+    ib = np.tile(np.arange(len(lb)), len(la)).astype(np.int32)
+    got_band, st = _run(lambda: eap.eap_pairs(p, A, B, ia, ib, with_stats=True), True)
+    got_panel = _run(lambda: eap.eap_pairs(p, A, B, ia, ib), False)
+    got_band = got_band.cpu().numpy()
+    got_panel = got_panel.cpu().numpy()
+    assert np.array_equal(got_band, got_panel), (kind, cost, w, np.flatnonzero(got_band != got_panel)[:5])
+    D = O.cross(oracle_params(kind, **kw), Ap, Bp)
+    for k in range(len(ia)):
+        d = float(D[ia[k], ib[k]])
+        if np.isinf(d):
+            assert np.isinf(got_band[k]), (kind, cost, w, k)
+        else:
+            assert close(float(got_band[k]), d), (kind, cost, w, k, got_band[k], d)
+    assert st["pairs"] == len(ia)
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+def test_band_nn1_base_matches_panels(eap, kind):
+    rng = np.random.default_rng(77 + (kind == "erp"))
+    qlen = list(rng.integers(100, 140, size=12))
+    rlen = list(rng.integers(100, 140, size=50))
+    Qp = synth.ragged_walks(len(qlen), qlen, 311, n_classes=3)
+    Rp = synth.ragged_walks(len(rlen), rlen, 312, n_classes=3)
+    Q, R = eap.SeriesSet.from_packed(Qp), eap.SeriesSet.from_packed(Rp)
+    kw = {"window_ratio": 0.15}
+    p = gpu_params(eap, kind, prune=0, **kw)
+    i1, d1 = _run(lambda: eap.eap_nn1(p, Q, R), True)
+    i0, d0 = _run(lambda: eap.eap_nn1(p, Q, R), False)
+    assert np.array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+    assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+    D = O.cross(oracle_params(kind, **kw), Qp, Rp)
+    check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+def test_band_pairwise_base_matches_panels(eap, kind):
+    x = synth.random_walks(np.random.default_rng(5), 24, 300).astype(np.float32)
+    S = eap.SeriesSet.from_matrix(x)
+    p = gpu_params(eap, kind, window=20, cost=1 if kind == "erp" else 0)
+    m1 = _run(lambda: eap.eap_pairwise(p, S, mode=eap.EAP_BASE), True).cpu().numpy()
+    m0 = _run(lambda: eap.eap_pairwise(p, S, mode=eap.EAP_BASE), False).cpu().numpy()
+    assert np.array_equal(m1, m0)
+
+
+def test_band_cells_and_workload_sample(eap):
+    """1000 x 1000 x 512 CDTW (w = 51): one band row of 112 cells per series
+    row, and sampled 1-NN equal to the oracle."""
+    ds = synth.workload_nn1_512()
+    tr, te = synth.pack(ds.train), synth.pack(ds.test)
+    R, Q = eap.SeriesSet.from_packed(tr), eap.SeriesSet.from_packed(te)
+    p = gpu_params(eap, "cdtw", prune=0, window_ratio=0.1)
+    idx, dist, st = eap.eap_nn1(p, Q, R, with_stats=True)
+    assert st["pairs"] == 1000 * 1000
+    assert st["cells_computed"] == 1000 * 1000 * 512 * 112
+    rows = list(np.random.default_rng(11).choice(1000, size=6, replace=False))
+    D = O.cross(oracle_params("cdtw", window_ratio=0.1), synth.pack([ds.test[r] for r in rows]), tr)
+    check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D, rows=rows)
