@@ -456,8 +456,11 @@ void choose_band(int kind, int prune, const KParams& kp, int max_rows, int max_c
     else return;
     const long long B = 2 * w + 3;
     if (B > L) return;
-    static const int kBands[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};   // (W, G)
-    for (const auto& b : kBands) {
+    static const int kBands8[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};     // (W, G)
+    static const int kBands16[][2] = {{4, 8}, {4, 16}, {7, 16}, {8, 16}, {16, 16}};
+    const char* g = std::getenv("EAP_BAND_G");
+    const bool g16 = g && std::atoi(g) == 16;
+    for (const auto& b : (g16 ? kBands16 : kBands8)) {
         if ((long long)b[0] * b[1] >= B) {
             *W = b[0];
             *G = b[1];

@@ -16,7 +16,8 @@
 // neighbour (shuffle down), then computes the other cells, and the last
 // cell reaches the right neighbour (shuffle up) for the next step.  A cell's
 // column j = i + k - w - 1 grows by one per row, so the column constants move
-// one cell to the left per step and each lane loads one new column per step.
+// one cell to the left per step and each lane loads one new column per step
+// (from L1: a shuffle from the right neighbour measured slower).
 //
 // Cells outside the series (j < 1 or j > L_B) see the column value +inf:
 // their point cost is +inf.  The recurrence then gives +inf everywhere it
@@ -33,8 +34,13 @@
 
 namespace eapd {
 
+#ifndef EAP_BAND_MINB
+#define EAP_BAND_MINB 0
+#endif
+
+
 template <class F, int W, int G>
-__global__ void __launch_bounds__(kThreads) band_dp_kernel(const DPJob job, const KParams kp) {
+__global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const DPJob job, const KParams kp) {
     static_assert(G == 8 || G == 16 || G == 32, "group width");
     static_assert(W >= 2, "strip width");
     constexpr int P = G * W;   // band cells per row
@@ -110,23 +116,27 @@ __global__ void __launch_bounds__(kThreads) band_dp_kernel(const DPJob job, cons
                     rc = F::row(s_next, 0.f, kp, nullptr);
                     if (act) s_next = __ldg(A + min(i, La - 1));
                 }
+                // The +inf addend right of the window stays off the row's
+                // left-to-right chain: the cells it applies to are a suffix of
+                // the row, so a masked cell's right neighbour is masked too.
                 float nv[W];
-                nv[0] = __fadd_rn(F::cell(v[0], v[1], x, rc, cc[0], 0, 0.f, kp), msk[0]);
-                if (gl == 0 && i >= w + 2) nv[0] = EAP_FINF;   // (i, i - w - 1): left of the window
+                float lf = F::cell(v[0], v[1], x, rc, cc[0], 0, 0.f, kp);
+                if (gl == 0 && i >= w + 2) lf = EAP_FINF;   // (i, i - w - 1): left of the window
+                nv[0] = __fadd_rn(lf, msk[0]);
                 const float pub = act ? nv[0] : v[0];
                 float y = __shfl_down_sync(gmask, pub, 1, G);
                 if (gl == G - 1) y = EAP_FINF;
 #pragma unroll
-                for (int u = 1; u < W; ++u)
-                    nv[u] = __fadd_rn(F::cell(v[u], u + 1 < W ? v[u + 1] : y, nv[u - 1], rc, cc[u], 0, 0.f, kp),
-                                      msk[u]);
+                for (int u = 1; u < W; ++u) {
+                    lf = F::cell(v[u], u + 1 < W ? v[u + 1] : y, lf, rc, cc[u], 0, 0.f, kp);
+                    nv[u] = __fadd_rn(lf, msk[u]);
+                }
                 if (act) {
 #pragma unroll
                     for (int u = 0; u < W; ++u) v[u] = nv[u];
 #pragma unroll
                     for (int u = 0; u + 1 < W; ++u) cc[u] = cc[u + 1];
                     cc[W - 1] = column(i + 1 + c0 + W - 1 - w - 1);   // column of the last cell in row i + 1
-                    cells += W;
                 }
             };
             const int nsteps = La + G - 1;
@@ -140,13 +150,14 @@ __global__ void __launch_bounds__(kThreads) band_dp_kernel(const DPJob job, cons
                 for (int k = 0; k < W; ++k) step(s + k, BoolC<false>{});
             }
             for (; s <= nsteps; ++s) step(s, BoolC<true>{});
+            cells += (unsigned long long)La * W;
             // M(L_A, L_B) sits at k = L_B - L_A + w + 1.
             const int kf = Lb - La + w + 1;
-            const int lf = kf / W, uf = kf - lf * W;
+            const int lane_f = kf / W, uf = kf - lane_f * W;
             float r = EAP_FINF;
 #pragma unroll
             for (int u = 0; u < W; ++u) if (u == uf) r = v[u];
-            d = __shfl_sync(gmask, r, lf, G);
+            d = __shfl_sync(gmask, r, lane_f, G);
         }
         if (gl == 0) {
             ++npairs;

@@ -224,8 +224,11 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
                 if (c.band == 8) return run_band<F, 8, 8>(d);
                 if (c.band == 14) return run_band<F, 14, 8>(d);
                 if (c.band == 16) return run_band<F, 16, 8>(d);
-            } else if (c.band_g == 16 && c.band == 16) {
-                return run_band<F, 16, 16>(d);
+            } else if (c.band_g == 16) {
+                if (c.band == 4) return run_band<F, 4, 16>(d);
+                if (c.band == 7) return run_band<F, 7, 16>(d);
+                if (c.band == 8) return run_band<F, 8, 16>(d);
+                if (c.band == 16) return run_band<F, 16, 16>(d);
             }
             return (int)cudaErrorInvalidValue;
         }
