@@ -438,15 +438,15 @@ int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int 
     return 0;
 }
 
-// Band mapping (band_dp_kernel) for the Base DP of CDTW and ERP: a row of the
-// window, plus the two border cells it reaches, is 2w + 3 cells; the
-// narrowest built launch that holds the widest pair's band is taken, if the
-// band is narrower than the series (else the column-panel kernels do less
-// work).  EAP_BAND=0 turns it off.
+// Band mapping (band_dp_kernel) for the Base and EAPruned DP of CDTW and ERP:
+// a row of the window, plus the two border cells it reaches, is 2w + 3
+// cells; the narrowest built launch that holds the widest pair's band is
+// taken, if the band is narrower than the series (else the column-panel
+// kernels do less work).  EAP_BAND=0 turns it off.
 void choose_band(int kind, int prune, const KParams& kp, int max_rows, int max_cols, int* W, int* G) {
     *W = 0;
     *G = 0;
-    if (prune != kPmBase || (kind != EAP_CDTW && kind != EAP_ERP)) return;
+    if ((prune != kPmBase && prune != kPmPruned) || (kind != EAP_CDTW && kind != EAP_ERP)) return;
     const char* e = std::getenv("EAP_BAND");
     if (e && std::atoi(e) == 0) return;
     const int L = max_rows > max_cols ? max_rows : max_cols;

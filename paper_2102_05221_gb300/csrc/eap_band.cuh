@@ -1,5 +1,6 @@
-// eap_band.cuh -- the Base DP (Alg. 3: every cell, no cut-off) of a windowed
-// distance (CDTW, ERP) in band coordinates.
+// eap_band.cuh -- the DP of a windowed distance (CDTW, ERP) in band
+// coordinates: Base (Alg. 3, every cell) and, with a cut-off, early
+// abandoning with the EAPruned result contract.
 //
 // Cell (i, j) of the window |i - j| <= w, together with the two border cells
 // that Section 2.3.2's computed borders reach (M(w+1, 0) and M(0, w+1)), is
@@ -28,6 +29,18 @@
 // window).  Row 0 holds M(0, 0) = 0 and the horizontal border.  Every cell
 // applies the distance's own cell() to the same predecessor values as the
 // other Base kernels, so the results are bit-identical to theirs.
+//
+// With a cut-off (PM = kPmPruned: 1-NN with the shared best-so-far, or
+// explicit per-item cut-offs) the kernel abandons a pair as soon as every
+// cell of the wavefront's current cut exceeds the cut-off, and returns
+// D(A, B) when D <= cut-off, else +inf -- the EAPruned contract.  The cut is
+// each lane's newest row: a path leaving the computed region does so from a
+// lane's newest row (the left lane is a row ahead, so a vertical step into it
+// stays inside; a horizontal step into the right lane, a row behind, leaves
+// from the newest row), so when all of them exceed the cut-off, so does D
+// (Alg. 4's abandoning test on this cut).  Pruning inside a row (Alg. 5's
+// skipped cells) would save no work here: the lanes compute the band row in
+// lock-step either way.
 #pragma once
 
 #include "eap_device.cuh"
@@ -39,16 +52,18 @@ namespace eapd {
 #endif
 
 
-template <class F, int W, int G>
+template <class F, int W, int G, int PM>
 __global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const DPJob job, const KParams kp) {
     static_assert(G == 8 || G == 16 || G == 32, "group width");
     static_assert(W >= 2, "strip width");
+    static_assert(PM == kPmBase || PM == kPmPruned, "mode");
+    constexpr bool CUT = PM == kPmPruned;
     constexpr int P = G * W;   // band cells per row
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const unsigned gmask = group_mask<G>(lane);
     const int c0 = gl * W;     // first band cell of this lane
-    unsigned long long cells = 0, npairs = 0, nerr = 0;
+    unsigned long long cells = 0, npairs = 0, nab = 0, nlb = 0, nerr = 0;
 
     for (;;) {
         unsigned long long it = 0;
@@ -71,6 +86,29 @@ __global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const 
         const float* B = job.B.data + ob;
         const float* bB = job.B.border ? job.B.border + ob : nullptr;
         const float4* rp = job.rowpack ? job.rowpack + oa : nullptr;
+        // Cut-off: the pair's own (Prune, explicit pairs) or the query's
+        // shared best-so-far (1-NN), refreshed at every abandoning test.
+        float cut = EAP_FINF;
+        const unsigned long long* cut_src = nullptr;
+        if (CUT) {
+            if (job.mode == kModeNN1) {
+                if (job.cut) {
+                    cut = __ldg(job.cut + (size_t)ai * job.B.n + bi);
+                } else {
+                    cut_src = job.best + ai;
+                    unsigned long long cv = 0;
+                    if (gl == 0) cv = *(volatile const unsigned long long*)cut_src;
+                    cv = __shfl_sync(gmask, cv, 0, G);
+                    cut = __uint_as_float((unsigned)(cv >> 32));
+                    if (job.lb && __ldg(job.lb + (size_t)ai * job.B.n + bi) > cut) {   // Alg. 2
+                        if (gl == 0) ++nlb;
+                        continue;
+                    }
+                }
+            } else if (job.cut) {
+                cut = __ldg(job.cut + it);
+            }
+        }
         const int La = __ldg(job.A.len + ai), Lb = __ldg(job.B.len + bi);
         const int w = pair_window(kp, La, Lb);
         float d = EAP_FINF;
@@ -139,28 +177,50 @@ __global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const 
                     cc[W - 1] = column(i + 1 + c0 + W - 1 - w - 1);   // column of the last cell in row i + 1
                 }
             };
+            // Abandoning test on the cut of each lane's newest row.
+            auto dead = [&]() -> bool {
+                if (cut_src) {
+                    unsigned long long cv = 0;
+                    if (gl == 0) cv = *(volatile const unsigned long long*)cut_src;
+                    cv = __shfl_sync(gmask, cv, 0, G);
+                    cut = fminf(cut, __uint_as_float((unsigned)(cv >> 32)));
+                }
+                float m = v[0];
+#pragma unroll
+                for (int u = 1; u < W; ++u) m = fminf(m, v[u]);
+                return (__ballot_sync(gmask, !(m > cut)) & gmask) == 0u;
+            };
             const int nsteps = La + G - 1;
             int s = 1;
+            bool ab = false;
             // Ramp-in: lanes start one step apart.
             for (; s < G && s <= nsteps; ++s) step(s, BoolC<true>{});
+            if (CUT) ab = dead();
             // Every lane active: steps G .. La, W at a time (the column
             // registers rotate back after W steps).
-            for (; s + W - 1 <= La; s += W) {
+            for (; !ab && s + W - 1 <= La; s += W) {
 #pragma unroll
                 for (int k = 0; k < W; ++k) step(s + k, BoolC<false>{});
+                if (CUT) ab = dead();
             }
-            for (; s <= nsteps; ++s) step(s, BoolC<true>{});
-            cells += (unsigned long long)La * W;
-            // M(L_A, L_B) sits at k = L_B - L_A + w + 1.
-            const int kf = Lb - La + w + 1;
-            const int lane_f = kf / W, uf = kf - lane_f * W;
-            float r = EAP_FINF;
+            if (!ab) {
+                for (; s <= nsteps; ++s) step(s, BoolC<true>{});
+            }
+            cells += (unsigned long long)max(0, min(La, s - 1 - gl)) * W;   // rows this lane computed
+            if (!ab) {
+                // M(L_A, L_B) sits at k = L_B - L_A + w + 1.
+                const int kf = Lb - La + w + 1;
+                const int lane_f = kf / W, uf = kf - lane_f * W;
+                float r = EAP_FINF;
 #pragma unroll
-            for (int u = 0; u < W; ++u) if (u == uf) r = v[u];
-            d = __shfl_sync(gmask, r, lane_f, G);
+                for (int u = 0; u < W; ++u) if (u == uf) r = v[u];
+                d = __shfl_sync(gmask, r, lane_f, G);
+                if (CUT && !(d <= cut)) d = EAP_FINF;
+            }
         }
         if (gl == 0) {
             ++npairs;
+            nab += (CUT && d == EAP_FINF) ? 1 : 0;
             if (job.mode == kModeNN1) {
                 if (d != EAP_FINF) atomicMin(job.best + ai, pack_best(d, (unsigned)bi));
             } else if (job.mode == kModePairwise) {
@@ -178,11 +238,15 @@ __global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const 
         for (int o = G / 2; o > 0; o >>= 1) {
             cells += __shfl_xor_sync(gmask, cells, o, G);
             npairs += __shfl_xor_sync(gmask, npairs, o, G);
+            nab += __shfl_xor_sync(gmask, nab, o, G);
+            nlb += __shfl_xor_sync(gmask, nlb, o, G);
             nerr += __shfl_xor_sync(gmask, nerr, o, G);
         }
         if (gl == 0) {
             if (npairs) atomicAdd(job.stats + kStatPairs, npairs);
+            if (nab) atomicAdd(job.stats + kStatAbandoned, nab);
             if (cells) atomicAdd(job.stats + kStatCells, cells);
+            if (nlb) atomicAdd(job.stats + kStatLbPruned, nlb);
             if (nerr) atomicAdd(job.stats + kStatErrors, nerr);
         }
     }

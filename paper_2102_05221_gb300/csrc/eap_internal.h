@@ -24,7 +24,7 @@ struct LaunchCtx {
     int max_rows;        // longest row series (sizes the per-warp shared column)
     int max_cols;        // longest column series (sizes the tiled bound kernel's shared tile)
     int cta;             // 1: CTA-per-pair mapping (long, unwindowed series); 0: warp per pair
-    int band = 0;        // Base DP of a windowed distance in band coordinates: strip width (0 = not used)
+    int band = 0;        // windowed DP in band coordinates (Base, EAPruned): strip width (0 = not used)
     int band_g = 0;      // lanes per pair of the band mapping
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
@@ -107,11 +107,13 @@ int run_dp(const LaunchCtx& c) {
     return (int)cudaGetLastError();
 }
 
-// Base DP of a windowed distance in band coordinates (band_dp_kernel), G lanes per pair.
+// DP of a windowed distance in band coordinates (band_dp_kernel): Base or
+// early abandoning (EAPruned contract), G lanes per pair.
 template <class F, int W, int G>
 int run_band(const LaunchCtx& c) {
     using namespace eapd;
-    void (*kern)(const DPJob, const KParams) = band_dp_kernel<F, W, G>;
+    void (*kern)(const DPJob, const KParams) =
+        c.prune == kPmPruned ? band_dp_kernel<F, W, G, kPmPruned> : band_dp_kernel<F, W, G, kPmBase>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     if (e != cudaSuccess) return (int)e;
@@ -218,7 +220,7 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     } else {
-        if (c.band && c.prune == eapd::kPmBase) {
+        if (c.band && (c.prune == eapd::kPmBase || c.prune == eapd::kPmPruned)) {
             if (c.band_g == 8) {
                 if (c.band == 4) return run_band<F, 4, 8>(d);
                 if (c.band == 8) return run_band<F, 8, 8>(d);

@@ -115,3 +115,83 @@ def test_band_cells_and_workload_sample(eap):
     rows = list(np.random.default_rng(11).choice(1000, size=6, replace=False))
     D = O.cross(oracle_params("cdtw", window_ratio=0.1), synth.pack([ds.test[r] for r in rows]), tr)
     check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D, rows=rows)
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+@pytest.mark.parametrize("w", [0, 3, 30, 54, 126])
+def test_band_eapruned_pairs_contract(eap, kind, w):
+    """Explicit cut-offs: D exactly when D <= cut-off, +inf above, and the
+    same outputs as the column-panel EAPruned kernel."""
+    rng = np.random.default_rng(4100 + w + (kind == "erp") * 500)
+    L = max(2 * w + 3, 48)
+    la = [L, L, L + w, max(1, L - w), L + 1, 2 * w + 3]
+    lb = [L, L + w, L, L, L, 2 * w + 3]
+    Ap = synth.ragged_walks(len(la), la, 1200 + w, n_classes=2)
+    Bp = synth.ragged_walks(len(lb), lb, 1201 + w, n_classes=2)
+    A, B = eap.SeriesSet.from_packed(Ap), eap.SeriesSet.from_packed(Bp)
+    kw = {"window": w}
+    ia = np.repeat(np.arange(len(la)), len(lb)).astype(np.int32)
+    ib = np.tile(np.arange(len(lb)), len(la)).astype(np.int32)
+    base = _run(lambda: eap.eap_pairs(gpu_params(eap, kind, prune=0, **kw), A, B, ia, ib), True).cpu().numpy()
+    p1 = gpu_params(eap, kind, prune=1, **kw)
+    fin = np.isfinite(base)
+    for scale in (0.0, 0.5, 0.9, 1.0, 1.1, 2.0):
+        cut = np.where(fin, np.where(fin, base, np.float32(0)) * np.float32(scale), np.float32(1.0)).astype(np.float32)
+        got, st = _run(lambda: eap.eap_pairs(p1, A, B, ia, ib, cut, with_stats=True), True)
+        ref = _run(lambda: eap.eap_pairs(p1, A, B, ia, ib, cut), False)
+        got, ref = got.cpu().numpy(), ref.cpu().numpy()
+        want = np.where(fin & (base <= cut), base, np.float32(np.inf))
+        assert np.array_equal(got, want), (kind, w, scale, np.flatnonzero(got != want)[:5])
+        assert np.array_equal(got, ref), (kind, w, scale)
+        if scale < 1.0 and fin.any() and w >= 3:
+            assert st["pairs_abandoned"] > 0
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+@pytest.mark.parametrize("prune", [1, 3])
+def test_band_eapruned_nn1_matches_panels_and_oracle(eap, kind, prune):
+    rng = np.random.default_rng(88 + prune + (kind == "erp"))
+    qlen = list(rng.integers(120, 160, size=10))
+    rlen = list(rng.integers(120, 160, size=60))
+    Qp = synth.ragged_walks(len(qlen), qlen, 611, n_classes=4)
+    Rp = synth.ragged_walks(len(rlen), rlen, 612, n_classes=4)
+    Q, R = eap.SeriesSet.from_packed(Qp), eap.SeriesSet.from_packed(Rp)
+    kw = {"window_ratio": 0.1}
+    p = gpu_params(eap, kind, prune=prune, **kw)
+    i1, d1, st = _run(lambda: eap.eap_nn1(p, Q, R, with_stats=True), True)
+    i0, d0 = _run(lambda: eap.eap_nn1(p, Q, R), False)
+    assert np.array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+    assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+    D = O.cross(oracle_params(kind, **kw), Qp, Rp)
+    check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
+    if prune == 1:
+        assert st["pairs_abandoned"] > 0
+
+
+def test_band_eapruned_lb_cascade(eap):
+    """CDTW with the LB_Keogh cascade ahead of the band kernel (Alg. 2)."""
+    ds = synth.make_dataset(200, 40, 256, 5, 97)
+    R, Q = eap.SeriesSet.from_matrix(ds.train), eap.SeriesSet.from_matrix(ds.test)
+    p = gpu_params(eap, "cdtw", prune=1, window_ratio=0.1, lb=2)
+    i1, d1, st = _run(lambda: eap.eap_nn1(p, Q, R, with_stats=True), True)
+    i0, d0 = _run(lambda: eap.eap_nn1(p, Q, R), False)
+    assert np.array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+    assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+    assert st["pairs_lb_pruned"] > 0
+
+
+def test_band_eapruned_workload_sample(eap):
+    """1000 x 1000 x 512 ERP and CDTW, EAPruned in band coordinates: 1-NN
+    equal to the column-panel kernel's and, on sampled queries, the oracle."""
+    ds = synth.workload_nn1_512()
+    tr, te = synth.pack(ds.train), synth.pack(ds.test)
+    R, Q = eap.SeriesSet.from_packed(tr), eap.SeriesSet.from_packed(te)
+    for kind, kw in (("erp", {"erp_gap": 0.0, "window_ratio": 0.1}), ("cdtw", {"window_ratio": 0.1})):
+        p = gpu_params(eap, kind, prune=1, **kw)
+        i1, d1 = _run(lambda: eap.eap_nn1(p, Q, R), True)
+        i0, d0 = _run(lambda: eap.eap_nn1(p, Q, R), False)
+        assert np.array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+        assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+        rows = list(np.random.default_rng(13).choice(1000, size=5, replace=False))
+        D = O.cross(oracle_params(kind, **kw), synth.pack([ds.test[r] for r in rows]), tr)
+        check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D, rows=rows)
