@@ -52,10 +52,14 @@ N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # DRAM bytes (read + write) of the dominant DP launch on this workload, from
 # one ncu capture (profiles/group_dp_kernel_msm_nn1_512_traffic.md), valid only for
 # the library build whose source fingerprint is recorded with it.
-# The EAPruned DP launch of this workload (L = 512) for its dominant distance: 16 lanes per pair, W = 5.
-DP_KERNEL = "group_dp_kernel<{}, W=5, G=16>"
-TRAFFIC = {"kernel": "group_dp_kernel<msm, W=5, G=16>", "bytes": 14858496,
-           "fingerprint": "3d53eea8920c675bd0a8c3b2603812eb8d46582becb5f52c97a78ca94bd687ef"}
+# The EAPruned DP launch of this workload (L = 512) per distance: 16 lanes per
+# pair over column panels (W = 5, WDTW 4), CDTW and ERP in band coordinates
+# (8 lanes x 14 cells per row).
+DP_KERNELS = {"dtw": "group_dp_kernel<dtw, W=5, G=16>", "wdtw": "group_dp_kernel<wdtw, W=4, G=16>",
+              "msm": "group_dp_kernel<msm, W=5, G=16>", "twe": "group_dp_kernel<twe, W=5, G=16>",
+              "cdtw": "band_dp_kernel<cdtw, W=14, G=8>", "erp": "band_dp_kernel<erp, W=14, G=8>"}
+TRAFFIC = {"kernel": "group_dp_kernel<msm, W=5, G=16>", "bytes": 14809600,
+           "fingerprint": "90d05b5c9c76eead2e02570ce9c5ea2f43cfce09fe8e1a14ac982ad25ec037a3"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"
 UNIT = "queries/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -393,11 +397,11 @@ def main():
     traffic = None
     try:
         from paper_2102_05221_gb300 import build as _b
-        if TRAFFIC["kernel"] == DP_KERNEL.format(dom) and TRAFFIC["fingerprint"] == _b._fingerprint():
+        if TRAFFIC["kernel"] == DP_KERNELS[dom] and TRAFFIC["fingerprint"] == _b._fingerprint():
             traffic = TRAFFIC["bytes"]
     except Exception:
         traffic = None
-    roofline = {"bound": "alu", "kernel": DP_KERNEL.format(dom), "achieved": achieved, "peak": peak,
+    roofline = {"bound": "alu", "kernel": DP_KERNELS[dom], "achieved": achieved, "peak": peak,
                 "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "work_basis": f"{OPS_PER_CELL[dom]} FP32 ops per computed cell"}
@@ -488,7 +492,7 @@ def workload_unpruned_512(args):
 
 def workload_modes_512(args):
     """Base, Prune, EABase and EAPruned 1-NN (the four implementations of the
-    paper's NN experiment, Section 4.1) on the 1000 x 1000 x 512 workload:
+    paper's NN experiment, Section 5.1) on the 1000 x 1000 x 512 workload:
     whole eap_nn1 calls (upper bounds, sort and DP) timed with CUDA events,
     L2 flushed before each call."""
     import statistics
@@ -531,12 +535,12 @@ def workload_modes_512(args):
             "speedup_all": {"vs_base": total["base"] / e, "vs_eabase": total["eabase"] / e,
                             "vs_prune": total["prune"] / e},
             "paper_cpu_context": {"vs_base": 7.61, "vs_eabase": 2.86,
-                                  "note": "UCR archive, 85 datasets, one Opteron core (Section 4.1)"},
+                                  "note": "UCR archive, 85 datasets, one Opteron core (Section 5.1)"},
             "per_distance": out}
 
 
 def workload_subseq(args):
-    """Sub-sequence search (Section 4.3): a 16M-point series, queries of 128 to
+    """Sub-sequence search (Section 5.3): a 16M-point series, queries of 128 to
     1024 points planted with N(0, 0.1) noise, CDTW (10% window) and DTW."""
     import time
 

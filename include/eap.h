@@ -58,7 +58,7 @@ typedef enum { EAP_DTW = 0, EAP_CDTW = 1, EAP_WDTW = 2, EAP_ERP = 3, EAP_MSM = 4
 typedef enum { EAP_COST_DEFAULT = -1, EAP_COST_SQ = 0, EAP_COST_ABS = 1 } eap_cost;
 
 /* Optional lower-bound cascade ahead of the DP (Alg. 2; LB_Keogh of
- * Section 4.2).  Only for DTW/CDTW with equal-length series; ignored otherwise. */
+ * Section 5.2).  Only for DTW/CDTW with equal-length series; ignored otherwise. */
 typedef enum { EAP_LB_NONE = 0, EAP_LB_KEOGH = 1, EAP_LB_KEOGH2 = 2 } eap_lb;
 
 typedef struct {
@@ -134,7 +134,7 @@ typedef struct {
  *   out_idx       : device int32[queries->count]; -1 when no candidate is finite.
  *   out_dist      : device float[queries->count]; +inf when none.
  * The cut-off starts at the smallest diagonal-path cost of the query over all
- * candidates (a valid upper bound, Section 3 intro), candidates are evaluated
+ * candidates (a valid upper bound, Section 4 intro), candidates are evaluated
  * nearest-diagonal-cost first, and concurrent candidates of one query share
  * the cut-off through a packed 64-bit atomicMin. */
 int eap_nn1(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs,
@@ -148,7 +148,7 @@ int eap_nn1_host(const eap_params* p,
                  const float* r_data, const int64_t* r_offsets, const int32_t* r_lengths, int32_t nr,
                  int32_t* out_idx, float* out_dist, eap_stats* opt_stats);
 
-#define EAP_PRUNE_ONLY 0   /* EAPruned with each pair's own diagonal-path cost as cut-off: exact, prunes but never abandons (Section 3 intro) */
+#define EAP_PRUNE_ONLY 0   /* EAPruned with each pair's own diagonal-path cost as cut-off: exact, prunes but never abandons (Section 4 intro) */
 #define EAP_BASE       1   /* plain Base DP (Alg. 3) */
 
 /* All-pairs distance matrix of one set: out_matrix is device float
@@ -170,7 +170,7 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
               void* cuda_stream, eap_stats* opt_stats);
 
 /* LB_Keogh(A_ia[k], B_ib[k]) for n pairs of equal length (textbook form,
- * Section 4.2): the envelope of A_ia[k] with window w = floor(ratio * L) (or
+ * Section 5.2): the envelope of A_ia[k] with window w = floor(ratio * L) (or
  * the absolute window) bounds the points of B_ib[k].  Squared or absolute
  * cost as the parameters say.  out: device float[n]; pairs whose lengths
  * differ get 0 (no bound). */
@@ -208,7 +208,7 @@ int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, const eap_se
                       void* cuda_stream, eap_stats* opt_stats);
 
 /* ---- sub-sequence search ---------------------------------------------------
- * Sub-sequence search (Section 4.3): for every query Q_q, the start position
+ * Sub-sequence search (Section 5.3): for every query Q_q, the start position
  * i in [0, n - L_q] of the long series `ref` that minimises
  * D(znorm(Q_q), znorm(ref[i .. i + L_q - 1])), D = DTW or CDTW (p->kind;
  * window w = floor(window_ratio * L_q) or p->window), computed with

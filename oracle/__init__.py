@@ -139,7 +139,7 @@ def eabase(params: OrcParams, s, t, cutoff: float):
 
 
 def subseq(params: OrcParams, T, q, nthreads: int | None = None):
-    """Sub-sequence search (Section 4.3): (position, distance) of the window
+    """Sub-sequence search (Section 5.3): (position, distance) of the window
     of T closest to q, both z-normalised; (-1, inf) if q is longer than T."""
     T, q = _f32(T), _f32(q)
     pos = ctypes.c_int64(-1)

@@ -18,14 +18,14 @@
  *                  arithmetic and its order are the definition's.
  *   orc_eapruned   Algorithm 5 (generic EAPruned) step by step in the paper's
  *                  stages, with a counter of computed cells (used to pin the
- *                  paper's worked-example counts, Section 3.2).
+ *                  paper's worked-example counts, Section 4.2).
  *   orc_eabase     Algorithm 4 (Base with a window and the usual early
  *                  abandoning on the row minimum), with a cell counter.
  *   orc_nn1        Algorithm 1 (NN search) over candidates in index order with
  *                  the strict "<" update; threads split the queries.
  *   orc_pairwise   the full distance matrix (the exact values that prune-only
- *                  mode must reproduce, Section 3 intro).
- *   orc_subseq     sub-sequence search (Section 4.3): every z-normalised
+ *                  mode must reproduce, Section 4 intro).
+ *   orc_subseq     sub-sequence search (Section 5.3): every z-normalised
  *                  window of a long series against a z-normalised query.
  *   orc_envelope / orc_lb_keogh   the textbook LB_Keogh (Section 2.1, Section
  *                  4.2): windowed min/max envelope, then the sum of the costs
@@ -221,7 +221,7 @@ static double orc_distance_d(const orc_params* p, const double* s0, int ls, cons
  * value exceeds the cut-off (the top border is monotone, Eq. Common).  For
  * +inf borders this is 1, as printed; for ERP's computed border it is the
  * first dead border index (the paper defines pruning points as the start of
- * a dead block reaching the end of the row, Section 3.2).
+ * a dead block reaching the end of the row, Section 4.2).
  * ------------------------------------------------------------------------ */
 typedef struct {
     const orc_params* p;
@@ -524,7 +524,7 @@ int orc_pairwise(const orc_params* p, const float* d, const int64_t* o, const in
  * each point of C that lies outside it to the nearest envelope edge.
  * ------------------------------------------------------------------------ */
 /* ------------------------------------------------------------------------
- * Sub-sequence search (Section 4.3): the start position i of the window of
+ * Sub-sequence search (Section 5.3): the start position i of the window of
  * the long series T that minimises D(znorm(Q), znorm(T[i .. i+m-1])).
  * z-normalisation: subtract the mean, divide by the population standard
  * deviation (two passes, in double); a window whose deviation is at most

@@ -189,7 +189,7 @@ __global__ void lb_keogh_pairs_kernel(const SeriesDev A, const SeriesDev B, cons
     }
 }
 
-// Envelope of every series for LB_Keogh (Section 4.2): U[k] / Lo[k] = max /
+// Envelope of every series for LB_Keogh (Section 5.2): U[k] / Lo[k] = max /
 // min of x over |m - k| <= w, w the pair window of an equal-length pair.
 __global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict__ U, float* __restrict__ Lo) {
     const int s = blockIdx.x;
@@ -212,7 +212,7 @@ __global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict
 
 // Lower bound of every (query, candidate) pair, [q][c]: LB_Keogh(Q, C) (the
 // query's envelope bounds C), and with two_way also LB_Keogh(C, Q); the
-// larger one is kept (the lb-keogh2 cascade of Section 4.2 in one pass).
+// larger one is kept (the lb-keogh2 cascade of Section 5.2 in one pass).
 // Pairs of unequal length get 0.  The bound is shrunk by `shrink` so float
 // rounding can never lift it above the float32 DP value of the pair.
 __global__ void lb_matrix_kernel(const SeriesDev Q, const SeriesDev R, const float* __restrict__ qU,
@@ -438,35 +438,51 @@ int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int 
     return 0;
 }
 
-// Band mapping (band_dp_kernel) for the Base and EAPruned DP of CDTW and ERP:
-// a row of the window, plus the two border cells it reaches, is 2w + 3
-// cells; the narrowest built launch that holds the widest pair's band is
-// taken, if the band is narrower than the series (else the column-panel
-// kernels do less work).  EAP_BAND=0 turns it off.
-void choose_band(int kind, int prune, const KParams& kp, int max_rows, int max_cols, int* W, int* G) {
+// Band mapping (band_dp_kernel) for the DP of CDTW and ERP in every mode
+// (Base; EAPruned and EABase abandon on the band's cut, and the lanes compute
+// whole band rows either way): a row of the window, plus the two border cells
+// it reaches, is 2w + 3 cells, and the narrowest built launch that holds the
+// widest pair's band is taken.  A launch is sized for the widest band, so it
+// is used only where every pair fills at least half of it and every series
+// is at least as long as the widest band (else the column-panel kernels do
+// less work).  EAP_BAND=0 turns it off, EAP_BAND=2 takes it whenever the band
+// fits a launch (tests).
+void choose_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G) {
     *W = 0;
     *G = 0;
-    if ((prune != kPmBase && prune != kPmPruned) || (kind != EAP_CDTW && kind != EAP_ERP)) return;
+    if (kind != EAP_CDTW && kind != EAP_ERP) return;
+    if (prune != kPmBase && prune != kPmPruned && prune != kPmEA) return;
     const char* e = std::getenv("EAP_BAND");
-    if (e && std::atoi(e) == 0) return;
-    const int L = max_rows > max_cols ? max_rows : max_cols;
-    long long w;
-    if (kp.window_abs >= 0) w = kp.window_abs;
-    else if (kp.window_ratio >= 0.f) w = (long long)std::floor((double)kp.window_ratio * (double)L);
-    else return;
-    const long long B = 2 * w + 3;
-    if (B > L) return;
+    const int mode = e ? std::atoi(e) : 1;
+    if (mode == 0) return;
+    auto window = [&](int L) -> long long {
+        if (kp.window_abs >= 0) return kp.window_abs;
+        if (kp.window_ratio >= 0.f) return (long long)std::floor((double)kp.window_ratio * (double)L);
+        return -1;
+    };
+    const long long w_hi = window(max_len), w_lo = window(min_len);
+    if (w_hi < 0) return;
+    const long long B = 2 * w_hi + 3;
     static const int kBands8[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};     // (W, G)
     static const int kBands16[][2] = {{4, 8}, {4, 16}, {7, 16}, {8, 16}, {16, 16}};
     const char* g = std::getenv("EAP_BAND_G");
     const bool g16 = g && std::atoi(g) == 16;
     for (const auto& b : (g16 ? kBands16 : kBands8)) {
-        if ((long long)b[0] * b[1] >= B) {
-            *W = b[0];
-            *G = b[1];
-            return;
-        }
+        const long long P = (long long)b[0] * b[1];
+        if (P < B) continue;
+        if (mode != 2 && (B > min_len || P > 2 * (2 * w_lo + 3))) return;
+        *W = b[0];
+        *G = b[1];
+        return;
     }
+}
+
+// Shortest series of a set (host mirror of the lengths); 0 for an empty set.
+int set_min_len(const eap_series_set* s) {
+    if (!s || s->count <= 0 || !s->h_lengths) return 0;
+    int m = s->h_lengths[0];
+    for (int i = 1; i < s->count; ++i) m = std::min(m, (int)s->h_lengths[i]);
+    return m;
 }
 
 // Strip width and lanes per pair together: W = 5 exists only for 16-lane
@@ -687,7 +703,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
     choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mr, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, mq, mr, &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -944,7 +960,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.max_cols = mx;
         c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
         c.group = c.cta ? 0 : choose_group(p->kind, cost, mx, mx, c.prune, c.W);
-        choose_band(p->kind, c.prune, c.kp, mx, mx, &c.band, &c.band_g);
+        choose_band(p->kind, c.prune, c.kp, set_min_len(set), mx, &c.band, &c.band_g);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -1037,7 +1053,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, ma, mb, &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1205,7 +1221,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.cost = cost;
     c.prune = p->prune;
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
-    choose_band(p->kind, c.prune, c.kp, ma, mb, &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g);
     c.sms = sms;
     c.max_rows = ma;
     c.max_cols = mb;
@@ -1263,8 +1279,8 @@ int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     return choose_group(kind, cost, max_rows, max_cols, prune, W);
 }
-void pick_band(int kind, int prune, const KParams& kp, int max_rows, int max_cols, int* W, int* G) {
-    choose_band(kind, prune, kp, max_rows, max_cols, W, G);
+void pick_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G) {
+    choose_band(kind, prune, kp, min_len, max_len, W, G);
 }
 
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {

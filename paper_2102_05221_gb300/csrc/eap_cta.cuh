@@ -19,7 +19,7 @@
 // No warp ever spins on another.
 //
 // Pruning: the pair is abandoned as soon as every lane's frontier is dead
-// (Section 3: no live cell can be reached), and a warp whose panel frontier is
+// (Section 4: no live cell can be reached), and a warp whose panel frontier is
 // dead while its left neighbour has finished stops that panel early (pruning
 // on the right); its consumer then reads +inf past the last live row.
 #pragma once

@@ -7,7 +7,7 @@
 //
 // Pruning on the GPU.  Alg. 5 prunes with left-to-right row scans
 // (next_start / pruning_point).  A warp cannot scan a row serially, so the
-// kernel uses the fact both of Alg. 5's strategies rest on (Section 3.1/3.2):
+// kernel uses the fact both of Alg. 5's strategies rest on (Section 4.1/4.2):
 // every step cost is >= 0, so a cell is never below its smallest dependency.
 // Hence (a) a cell whose dependencies all exceed the cut-off exceeds it too,
 // and (b) replacing any value above the cut-off by +inf changes no value at or
@@ -770,7 +770,7 @@ __device__ float warp_pair(const PairIn& in, float* __restrict__ bnd, const KPar
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal-path upper bound (Section 3 intro: any warping path's cost bounds
+// Diagonal-path upper bound (Section 4 intro: any warping path's cost bounds
 // D from above).  The path is (1,1)..(m,m), m = min(La,Lb), then straight
 // along the longer axis.  It is evaluated with the same functor as the DP,
 // with the off-path dependencies at +inf, so the DP's value is <= this bound

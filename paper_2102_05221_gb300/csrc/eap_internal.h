@@ -54,8 +54,9 @@ int pick_w(int kind, int cost, int max_cols, int prune);
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W);
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G);
-// Band mapping of the windowed Base DP: strip width and lanes per pair, or 0.
-void pick_band(int kind, int prune, const eapd::KParams& kp, int max_rows, int max_cols, int* W, int* G);
+// Band mapping of the windowed DP: strip width and lanes per pair, or 0
+// (min_len / max_len: shortest and longest series of the call).
+void pick_band(int kind, int prune, const eapd::KParams& kp, int min_len, int max_len, int* W, int* G);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).
@@ -107,13 +108,14 @@ int run_dp(const LaunchCtx& c) {
     return (int)cudaGetLastError();
 }
 
-// DP of a windowed distance in band coordinates (band_dp_kernel): Base or
-// early abandoning (EAPruned contract), G lanes per pair.
+// DP of a windowed distance in band coordinates (band_dp_kernel): Base, or
+// early abandoning for EAPruned and EABase (every cell of a row is computed
+// either way), G lanes per pair.
 template <class F, int W, int G>
 int run_band(const LaunchCtx& c) {
     using namespace eapd;
     void (*kern)(const DPJob, const KParams) =
-        c.prune == kPmPruned ? band_dp_kernel<F, W, G, kPmPruned> : band_dp_kernel<F, W, G, kPmBase>;
+        c.prune == kPmBase ? band_dp_kernel<F, W, G, kPmBase> : band_dp_kernel<F, W, G, kPmPruned>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     if (e != cudaSuccess) return (int)e;
@@ -220,7 +222,7 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
     if constexpr (!WIN) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     } else {
-        if (c.band && (c.prune == eapd::kPmBase || c.prune == eapd::kPmPruned)) {
+        if (c.band) {
             if (c.band_g == 8) {
                 if (c.band == 4) return run_band<F, 4, 8>(d);
                 if (c.band == 8) return run_band<F, 8, 8>(d);

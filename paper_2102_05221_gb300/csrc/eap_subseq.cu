@@ -1,4 +1,4 @@
-// eap_subseq.cu -- sub-sequence search under EAPruned DTW / CDTW (Section 4.3):
+// eap_subseq.cu -- sub-sequence search under EAPruned DTW / CDTW (Section 5.3):
 // the window of a long series closest to a query, both z-normalised.
 //
 // Per query of length m over a series of n points (npos = n - m + 1 windows):
@@ -77,7 +77,7 @@ __global__ void subseq_norm_kernel(const float* __restrict__ T, long long npos, 
 }
 
 // One block: the query normalised (two passes in double) and its envelope
-// over +-w (LB_Keogh, Section 4.2).
+// over +-w (LB_Keogh, Section 5.2).
 __global__ void subseq_query_kernel(const float* __restrict__ q, int m, int w, float* __restrict__ zq,
                                     float* __restrict__ U, float* __restrict__ L) {
     __shared__ double red[32];

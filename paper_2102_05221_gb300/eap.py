@@ -281,7 +281,7 @@ def eap_lb_keogh(p: eap_params, a: SeriesSet, b: SeriesSet, ia, ib, stream=None)
 
 
 def eap_subseq(p: eap_params, ref, queries: SeriesSet, stream=None, with_stats: bool = False):
-    """Sub-sequence search (Section 4.3): for every query, the start position
+    """Sub-sequence search (Section 5.3): for every query, the start position
     of the window of the long series `ref` (a 1-D float32 array or device
     tensor) closest to it under z-normalised DTW / CDTW.  Returns device
     tensors (pos int64, dist float32) [and the stats]."""

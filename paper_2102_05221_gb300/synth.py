@@ -1,7 +1,7 @@
 """Seeded synthetic time-series inputs shaped like the paper's workloads.
 
-The paper measures on the UCR archive (85 datasets, Section 4.1) and on the
-UCR-suite sub-sequence data (Section 4.3); neither is available here, so these
+The paper measures on the UCR archive (85 datasets, Section 5.1) and on the
+UCR-suite sub-sequence data (Section 5.3); neither is available here, so these
 generators stand in for them.  Every series is a z-normalised Gaussian random
 walk (step sigma = 1), optionally plus a class template
 ``sin(2*pi*f_k*t/L)`` with ``f_k = k + 1`` cycles, then z-normalised again
@@ -145,7 +145,7 @@ def uniform_values(n: int, lengths, seed: int, lo: float = -3.0, hi: float = 3.0
 
 def long_series(n: int, seed: int, seg=(200, 2000), n_classes: int = 10) -> np.ndarray:
     """A long series standing in for the references of sub-sequence search
-    (Section 4.3): back-to-back segments of log-uniform length in `seg`, each
+    (Section 5.3): back-to-back segments of log-uniform length in `seg`, each
     a z-normalised random walk plus a class sine template (values O(1))."""
     rng = _rng(seed)
     lo, hi = seg

@@ -1,6 +1,7 @@
 """Base DP of the windowed distances (CDTW, ERP) in band coordinates
-(band_dp_kernel): bit-identical to the column-panel Base kernels (the band
-mapping switched off with EAP_BAND=0) and within tolerance of the FP64
+(band_dp_kernel): bit-identical to the column-panel kernels (the band
+mapping forced with EAP_BAND=2, switched off with EAP_BAND=0) and within
+tolerance of the FP64
 oracle, on ragged lengths, windows at and around every built band width,
 the degenerate windows (w = 0, w = |L_A - L_B|) and the three entry points
 that run the Base DP (pairs, 1-NN with prune = 0, all-pairs matrix)."""
@@ -27,11 +28,10 @@ def eap():
 
 
 def _run(fn, band):
+    """Runs fn with the band mapping forced (EAP_BAND=2: whenever the band
+    fits a launch, even where the default keeps the panel kernels) or off."""
     old = os.environ.get("EAP_BAND")
-    if band:
-        os.environ.pop("EAP_BAND", None)
-    else:
-        os.environ["EAP_BAND"] = "0"
+    os.environ["EAP_BAND"] = "2" if band else "0"
     try:
         return fn()
     finally:
@@ -148,7 +148,7 @@ def test_band_eapruned_pairs_contract(eap, kind, w):
 
 
 @pytest.mark.parametrize("kind", ["cdtw", "erp"])
-@pytest.mark.parametrize("prune", [1, 3])
+@pytest.mark.parametrize("prune", [1, 2, 3])
 def test_band_eapruned_nn1_matches_panels_and_oracle(eap, kind, prune):
     rng = np.random.default_rng(88 + prune + (kind == "erp"))
     qlen = list(rng.integers(120, 160, size=10))
@@ -164,7 +164,7 @@ def test_band_eapruned_nn1_matches_panels_and_oracle(eap, kind, prune):
     assert np.array_equal(d1.cpu().numpy(), d0.cpu().numpy())
     D = O.cross(oracle_params(kind, **kw), Qp, Rp)
     check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
-    if prune == 1:
+    if prune in (1, 2):
         assert st["pairs_abandoned"] > 0
 
 
@@ -195,3 +195,18 @@ def test_band_eapruned_workload_sample(eap):
         rows = list(np.random.default_rng(13).choice(1000, size=5, replace=False))
         D = O.cross(oracle_params(kind, **kw), synth.pack([ds.test[r] for r in rows]), tr)
         check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D, rows=rows)
+
+
+def test_band_default_choice(eap):
+    """The default takes the band only where every series is at least as long
+    as the widest band row: a set with a short series keeps the panel kernels
+    (cells counted per band row would exceed the matrix)."""
+    rng = np.random.default_rng(3)
+    lens = [1, 5, 300] + list(rng.integers(200, 300, size=10))
+    Ap = synth.ragged_walks(len(lens), lens, 71, n_classes=2)
+    A = eap.SeriesSet.from_packed(Ap)
+    p = gpu_params(eap, "erp", prune=0, window_ratio=0.1)
+    ia = np.repeat(np.arange(len(lens)), len(lens)).astype(np.int32)
+    ib = np.tile(np.arange(len(lens)), len(lens)).astype(np.int32)
+    _, st = eap.eap_pairs(p, A, A, ia, ib, with_stats=True)
+    assert st["cells_computed"] <= st["cells_effective"]

@@ -1,4 +1,4 @@
-"""Sub-sequence search (Section 4.3) through the C ABI against the FP64
+"""Sub-sequence search (Section 5.3) through the C ABI against the FP64
 oracle: every z-normalised window of a long series, DTW and CDTW."""
 import math
 

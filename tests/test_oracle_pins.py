@@ -1,8 +1,8 @@
 """Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
 
 Each test ties the oracle to something other than itself: the paper's worked
-example (Fig. DTW, Section 3.2), brute-force enumeration of every alignment
-path, closed forms, and invariants the paper states (Section 2.3, Section 3).
+example (Fig. DTW, Section 4.2), brute-force enumeration of every alignment
+path, closed forms, and invariants the paper states (Section 2.3, Section 4).
 """
 import math
 import os
@@ -226,7 +226,7 @@ KIND_EA = ["dtw", "cdtw", "wdtw", "erp", "msm", "twe"]
 @pytest.mark.parametrize("kind", KIND_EA)
 def test_eapruned_returns_inf_exactly_when_distance_exceeds_cutoff(kind):
     """Algorithm 5 returns D when D <= cut-off and +inf otherwise (Section 2.2,
-    Section 3.3), for cut-offs on both sides of D."""
+    Section 4.3), for cut-offs on both sides of D."""
     x = synth.ragged_walks(10, [30, 30, 42, 25, 30, 55, 30, 31, 29, 44], 10)
     p = O.make_params(kind, window_ratio=0.2 if kind in ("cdtw", "erp") else -1)
     for i in range(0, x.count, 2):
@@ -244,7 +244,7 @@ def test_eapruned_returns_inf_exactly_when_distance_exceeds_cutoff(kind):
 
 
 def test_eapruned_complexity_depends_on_candidate_order():
-    # Section 3.3.1: nearest-first ordering leaves later candidates almost free;
+    # Section 4.3.1: nearest-first ordering leaves later candidates almost free;
     # furthest-first computes (almost) everything.
     ds = synth.make_dataset(20, 1, 64, 3, 123)
     q = ds.test[0]
@@ -488,7 +488,7 @@ def test_eabase_erp_row_minimum_includes_the_vertical_border():
 
 
 # ---------------------------------------------------------------------------
-# Sub-sequence search (Section 4.3): z-normalised windows of a long series.
+# Sub-sequence search (Section 5.3): z-normalised windows of a long series.
 
 def _znorm_np(x):
     x = np.asarray(x, dtype=np.float64)
