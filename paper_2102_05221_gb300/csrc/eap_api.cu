@@ -465,9 +465,13 @@ void choose_band(int kind, int prune, const KParams& kp, int min_len, int max_le
     const long long B = 2 * w_hi + 3;
     static const int kBands8[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};     // (W, G)
     static const int kBands16[][2] = {{4, 8}, {4, 16}, {7, 16}, {8, 16}, {16, 16}};
+    // 8 lanes per pair except for the abandoning ERP DP, whose wider cells
+    // need fewer per lane to keep registers and occupancy up (1000 x 1000 x
+    // 512, w = 51: ERP 11.0 -> 9.5 ms with 16 lanes x 7; CDTW and the Base DP
+    // are faster with 8 lanes).  EAP_BAND_G = 8 or 16 overrides.
     const char* g = std::getenv("EAP_BAND_G");
-    const bool g16 = g && std::atoi(g) == 16;
-    for (const auto& b : (g16 ? kBands16 : kBands8)) {
+    const int gsel = g ? std::atoi(g) : ((kind == EAP_ERP && prune != kPmBase) ? 16 : 8);
+    for (const auto& b : (gsel == 16 ? kBands16 : kBands8)) {
         const long long P = (long long)b[0] * b[1];
         if (P < B) continue;
         if (mode != 2 && (B > min_len || P > 2 * (2 * w_lo + 3))) return;
