@@ -87,6 +87,9 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 #ifndef EAP_X2_TWE
 #define EAP_X2_TWE EAP_X2
 #endif
+#ifndef EAP_X2_DTW
+#define EAP_X2_DTW EAP_X2
+#endif
 // Resident blocks per SM that group_dp_kernel asks the register allocator
 // for (strip widths up to 5; 0 leaves the choice to the compiler, which then
 // takes the fewest registers that do not spill).  With the group's cold state
@@ -152,7 +155,7 @@ struct FDtw {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;   // the row constant is s_i itself
-    static constexpr bool kX2 = false;
+    static constexpr bool kX2 = EAP_X2_DTW;
     static constexpr int kGroupBlocks = EAP_MINB_DTW;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
@@ -163,6 +166,30 @@ struct FDtw {
         const float m = min3f(dg, tp, lf);
         const float d = __fsub_rn(r.s, c.t);
         return COST == 0 ? __fmaf_rn(d, d, m) : __fadd_rn(fabsf(d), m);
+    }
+    // One row of a strip, cell() for every cell with the same operations;
+    // s_i - t_j runs on neighbouring cells in pairs.
+    template <int W, bool WIN>
+    __device__ static void strip(float (&v)[W], float (&)[W], const float (&wr)[W], const Col (&cc)[W],
+                                 const Row& rc, float dg, float lf, const KParams&) {
+        float d[W];
+#pragma unroll
+        for (int u = 0; u + 1 < W; u += 2) {
+            const float2 d2 = sub2_rn(make_float2(rc.s, rc.s), make_float2(cc[u].t, cc[u + 1].t));
+            d[u] = d2.x;
+            d[u + 1] = d2.y;
+        }
+        if constexpr (W % 2 == 1) d[W - 1] = __fsub_rn(rc.s, cc[W - 1].t);
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const float top = v[u];
+            const float m = min3f(dg, top, lf);
+            float nv = COST == 0 ? __fmaf_rn(d[u], d[u], m) : __fadd_rn(fabsf(d[u]), m);
+            if (WIN) nv = __fadd_rn(nv, wr[u]);
+            dg = top;
+            v[u] = nv;
+            lf = nv;
+        }
     }
 };
 
@@ -177,7 +204,7 @@ struct FWdtw {
     static constexpr bool kPen = false;
     static constexpr bool kBorders = false;
     static constexpr bool kPacked = false;
-    static constexpr bool kX2 = false;
+    static constexpr bool kX2 = EAP_X2_DTW;
     static constexpr int kGroupBlocks = EAP_MINB_WDTW;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
@@ -191,6 +218,35 @@ struct FWdtw {
     }
     __device__ static float cell_w(float dg, float tp, float lf, const Row& r, const Col& c, float wgt) {
         return __fmaf_rn(wgt, pcost<COST>(r.s, c.t), min3f(dg, tp, lf));
+    }
+    // One row of a strip, cell_w() for every cell with the same operations;
+    // s_i - t_j and the point cost run on neighbouring cells in pairs.
+    template <int W, bool WIN>
+    __device__ static void strip(float (&v)[W], float (&)[W], const float (&wr)[W], const Col (&cc)[W],
+                                 const Row& rc, float dg, float lf, const KParams&) {
+        static_assert(!WIN, "WDTW has no window");
+        float c[W];
+#pragma unroll
+        for (int u = 0; u + 1 < W; u += 2) {
+            const float2 d2 = sub2_rn(make_float2(rc.s, rc.s), make_float2(cc[u].t, cc[u + 1].t));
+            if constexpr (COST == 0) {
+                const float2 c2 = __fmul2_rn(d2, d2);
+                c[u] = c2.x;
+                c[u + 1] = c2.y;
+            } else {
+                c[u] = fabsf(d2.x);
+                c[u + 1] = fabsf(d2.y);
+            }
+        }
+        if constexpr (W % 2 == 1) c[W - 1] = pcost<COST>(rc.s, cc[W - 1].t);
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const float top = v[u];
+            const float nv = __fmaf_rn(wr[u], c[u], min3f(dg, top, lf));
+            dg = top;
+            v[u] = nv;
+            lf = nv;
+        }
     }
 };
 
