@@ -1,7 +1,9 @@
 """Randomised parity sweep: seeded random configurations (distance, cost,
 window, parameters, mode, derivative, lengths around the panel widths of
-every mapping) through eap_nn1 and eap_pairs against the FP64 oracle."""
+every mapping) through eap_nn1 and eap_pairs against the FP64 oracle; for
+CDTW and ERP also with the band mapping forced."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -72,6 +74,20 @@ def test_random_configuration_matches_oracle(seed):
     idx, dist = eap.eap_nn1(p, Q, R)
     D = O.cross(O.make_params(cfg["kind"], **cfg["orc"]), Qp, Rp)
     check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D)
+    if cfg["kind"] in ("cdtw", "erp"):
+        # The band mapping forced (it takes any band that fits a launch):
+        # the same 1-NN, bit for bit.
+        old = os.environ.get("EAP_BAND")
+        os.environ["EAP_BAND"] = "2"
+        try:
+            ib, db = eap.eap_nn1(p, Q, R)
+        finally:
+            if old is None:
+                os.environ.pop("EAP_BAND", None)
+            else:
+                os.environ["EAP_BAND"] = old
+        assert np.array_equal(ib.cpu().numpy(), idx.cpu().numpy()), cfg
+        assert np.array_equal(db.cpu().numpy(), dist.cpu().numpy()), cfg
     # Explicit pairs with cut-offs around the oracle's distances (EAPruned only).
     if cfg["gpu"]["prune"] == 1:
         ia = np.repeat(np.arange(nq), nr).astype(np.int32)
