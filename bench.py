@@ -187,8 +187,11 @@ def run_reference(args, rank, world):
     return 0
 
 
-def cpu_baseline(ds, budget_s: float):
-    """The oracle as it stands, timed on this host's cores on a bounded sample."""
+def cpu_baseline(ds, budget_s: float, n_test: int):
+    """The oracle as it stands, timed on this host's cores on a bounded sample:
+    full FP64 distance rows (plain definition, no pruning) of the first nq test
+    series against every train series, per distance.  Returns the baseline
+    entry and the rows (for the sampled parity check)."""
     import oracle as O
     from paper_2102_05221_gb300 import synth
     cores = os.cpu_count() or 1
@@ -197,18 +200,81 @@ def cpu_baseline(ds, budget_s: float):
     t0 = time.perf_counter()
     q1 = synth.pack([ds.test[0]])
     for kind, kw in KIND_PARAMS.items():
-        O.nn1(O.make_params(kind, **kw), q1, tr, nthreads=cores)
+        O.cross(O.make_params(kind, **kw), q1, tr, nthreads=cores)
     t1 = time.perf_counter() - t0
     per_q = t1 / len(KIND_PARAMS)   # one query on one thread ~ cores x this when threads split the queries
     nq = int(max(cores, min(256, budget_s / max(per_q, 1e-6) * cores / len(KIND_PARAMS))))
-    nq = (nq // cores) * cores or cores
-    q = synth.pack([ds.test[i % N_TEST] for i in range(nq)])
+    nq = min(n_test, (nq // cores) * cores or cores)
+    q = synth.pack([ds.test[i] for i in range(nq)])
+    rows = {}
     t0 = time.perf_counter()
     for kind, kw in KIND_PARAMS.items():
-        O.nn1(O.make_params(kind, **kw), q, tr, nthreads=cores)
+        rows[kind] = O.cross(O.make_params(kind, **kw), q, tr, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": nq * len(KIND_PARAMS) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nq} test series x 1000 train x 6 distances, FP64 oracle, {cores} threads, {dt:.1f} s"}
+    entry = {"value": nq * len(KIND_PARAMS) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"test series 0..{nq - 1} x 1000 train x 6 distances, FP64 oracle (full distance rows, "
+                       f"no pruning), {cores} threads, {dt:.1f} s"}
+    return entry, rows
+
+
+def cpu_alg5_baseline(ds, budget_s: float):
+    """The paper's own design on the CPU, like for like: Alg. 1 calling Alg. 5
+    (EAPruned, FP64) with the best-so-far as cut-off, candidates in index
+    order, ONE thread; whole rounds of one query per distance until the
+    budget is spent.  Returns the entry and the (index, distance) results."""
+    import oracle as O
+    from paper_2102_05221_gb300 import synth
+    tr = synth.pack(ds.train)
+    res = {k: [] for k in KIND_PARAMS}
+    t0 = time.perf_counter()
+    rounds, cells = 0, 0
+    while rounds == 0 or time.perf_counter() - t0 < budget_s:
+        q = synth.pack([ds.test[rounds]])
+        for kind, kw in KIND_PARAMS.items():
+            idx, dist, c = O.nn1_eapruned(O.make_params(kind, **kw), q, tr)
+            res[kind].append((int(idx[0]), float(dist[0])))
+            cells += c
+        rounds += 1
+    dt = time.perf_counter() - t0
+    entry = {"value": rounds * len(KIND_PARAMS) / dt, "unit": UNIT, "cores": 1, "kind": "oracle_alg5",
+             "sample": f"test series 0..{rounds - 1} x 1000 train x 6 distances, Alg. 1 + Alg. 5 (FP64, "
+                       f"cut-off = best so far, index order), one thread, {dt:.1f} s",
+             "cells_computed_over_effective": cells / (rounds * len(KIND_PARAMS) * N_TRAIN * LENGTH * LENGTH)}
+    return entry, res
+
+
+def sampled_parity(rows, out_idx, out_dist):
+    """GPU 1-NN results of the sampled test series against the oracle's full
+    distance rows: indices exact unless the oracle's top-2 gap is under
+    2e-4 relative (a near-tie: flagged and counted), distances within 1e-4
+    relative of FP64."""
+    import numpy as np
+    res = {"queries": 0, "index_mismatches": 0, "near_ties": 0, "near_tie_index_differs": 0,
+           "max_rel_err": 0.0, "tolerance_rel": 1e-4}
+    for kind, D in rows.items():
+        gi = out_idx[kind][:D.shape[0]].cpu().numpy()
+        gd = out_dist[kind][:D.shape[0]].cpu().numpy().astype(np.float64)
+        for q in range(D.shape[0]):
+            best = int(np.argmin(D[q]))
+            ref = float(D[q, best])
+            srt = np.sort(D[q])
+            tie = len(srt) > 1 and srt[1] - srt[0] <= 2e-4 * max(ref, 1e-30)
+            res["queries"] += 1
+            res["near_ties"] += int(tie)
+            if int(gi[q]) != best:
+                if tie:
+                    res["near_tie_index_differs"] += 1
+                else:
+                    res["index_mismatches"] += 1
+            res["max_rel_err"] = max(res["max_rel_err"], abs(float(gd[q]) - ref) / max(ref, 1e-30))
+    res["ok"] = res["index_mismatches"] == 0 and res["max_rel_err"] <= 1e-4
+    return res
+
+
+def _near_tie(row) -> bool:
+    import numpy as np
+    srt = np.sort(row)
+    return len(srt) > 1 and srt[1] - srt[0] <= 2e-4 * max(float(srt[0]), 1e-30)
 
 
 def main():
@@ -220,8 +286,13 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=0,
                     help="test series per step of the reference arm (0: one per host core)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--alg5-budget", type=float, default=8.0,
+                    help="seconds of the single-thread Alg. 1 + Alg. 5 CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-unpruned", action="store_true",
+                    help="skip the unpruned (Base) DP block of the benchmark line")
+    ap.add_argument("--unpruned-steps", type=int, default=2)
     ap.add_argument("--kinds", default=",".join(KIND_PARAMS),
                     help="subset of distances (profiling runs only; the benchmark is all six)")
     ap.add_argument("--n-test", type=int, default=N_TEST, help="test series per rank (profiling runs only)")
@@ -235,9 +306,22 @@ def main():
     kinds = [k for k in args.kinds.split(",") if k]
     n_test = args.n_test
 
+    if args.gpus < 1:
+        raise SystemExit("--gpus must be >= 1")
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # One process per GPU: re-launch this command under torchrun.
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+        return subprocess.call(cmd)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"bench.py --gpus {args.gpus} runs with WORLD_SIZE={world}: launch one rank per GPU")
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload != "nn1_512":
@@ -250,6 +334,8 @@ def main():
     from paper_2102_05221_gb300 import eap
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
+    if torch.cuda.device_count() <= local:
+        raise SystemExit(f"rank {rank}: LOCAL_RANK {local} but only {torch.cuda.device_count()} GPU(s) visible")
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
@@ -421,8 +507,31 @@ def main():
         line["e2e"] = e2e
     if kinds != list(KIND_PARAMS) or n_test != N_TEST:
         line["config"]["profiling_subset"] = {"kinds": kinds, "n_test": n_test}
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(ds, args.cpu_budget)
+    if not args.no_unpruned:
+        # Base (Alg. 3) DP of every distance on the same inputs: the ALU
+        # roofline of the unpruned recurrence, with its own clock record.
+        us = ClockSampler(local)
+        us.start()
+        time.sleep(0.3)
+        rows = unpruned_rows(eap, R, Q, LENGTH, kinds, args.unpruned_steps, 1, alu_peak_ops(
+            props.multi_processor_count, max_mhz), flush)
+        line["unpruned"] = {"workload": f"base_dp_{N_TRAIN}x{n_test}_L{LENGTH}", "per_distance": rows,
+                            "clocks": us.stop(),
+                            "basis": "algorithmic cells (windowed: |i-j| <= w only) x ops/cell / DP event time"}
+    if not args.no_cpu_baseline and world == 1 and kinds == list(KIND_PARAMS):
+        line["cpu_baseline"], orows = cpu_baseline(ds, args.cpu_budget, n_test)
+        line["parity_sample"] = sampled_parity(orows, out_idx, out_dist)
+        line["cpu_baseline_alg5"], a5 = cpu_alg5_baseline(ds, args.alg5_budget)
+        # The single-thread Alg. 5 search must agree with the GPU on its queries too.
+        a5_bad = 0
+        for k, lst in a5.items():
+            gi = out_idx[k].cpu().numpy()
+            gd = out_dist[k].cpu().numpy()
+            for q, (i5, d5) in enumerate(lst):
+                tie = q < orows[k].shape[0] and _near_tie(orows[k][q])
+                if abs(float(gd[q]) - d5) > 1e-4 * max(d5, 1e-30) or (int(gi[q]) != i5 and not tie):
+                    a5_bad += 1
+        line["cpu_baseline_alg5"]["disagreements_with_gpu"] = a5_bad
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -448,9 +557,44 @@ def _alu_peak(props):
     return alu_peak_ops(props.multi_processor_count, float(_peaks().get("sm_max_mhz", 2070.0)))
 
 
+def algorithmic_cells(kind: str, L: int) -> int:
+    """Cells of one L x L pair that the recurrence defines: every cell, or for
+    a windowed distance only those with |i - j| <= w."""
+    import numpy as np
+    if "window_ratio" in KIND_PARAMS[kind]:
+        w = int(math.floor(float(np.float32(KIND_PARAMS[kind]["window_ratio"])) * L))
+        return sum(min(L, i + w) - max(1, i - w) + 1 for i in range(1, L + 1))
+    return L * L
+
+
+def unpruned_rows(eap, R, Q, L, kinds, steps, warmup, peak, flush):
+    """Base (Alg. 3) 1-NN DP per distance on R x Q: DP time from the library's
+    CUDA events on the launching stream, L2 flushed before every call;
+    algorithmic cell updates/s and their fraction of the FP32 ALU roofline."""
+    out = {}
+    for k in kinds:
+        p = eap.params(k, prune=0, **KIND_PARAMS[k])
+        for _ in range(max(1, warmup)):
+            eap.eap_nn1(p, Q, R)
+        ms, cells = 0.0, 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
+            ms += st["dp_ms"]
+            cells += st["cells_computed"]
+        band = algorithmic_cells(k, L)
+        alg = band * R.count * Q.count * steps
+        rate = alg / (ms / 1e3)
+        out[k] = {"dp_ms": ms / steps, "cells_per_s": rate, "ops_per_cell": OPS_PER_CELL[k],
+                  "alu_frac": rate * OPS_PER_CELL[k] / peak,
+                  "cells_roofline_per_s": peak / OPS_PER_CELL[k],
+                  "algorithmic_cells_per_pair": band,
+                  "computed_cells_per_pair": cells / (steps * R.count * Q.count)}
+    return out
+
+
 def workload_unpruned_512(args):
     """Base (unpruned) DP on the 1000 x 1000 x 512 workload: the ALU roofline."""
-    import numpy as np
     import torch
 
     from paper_2102_05221_gb300 import eap
@@ -458,36 +602,13 @@ def workload_unpruned_512(args):
     R, Q = eap.SeriesSet.from_matrix(ds.train), eap.SeriesSet.from_matrix(ds.test)
     props = torch.cuda.get_device_properties(0)
     peak = _alu_peak(props)
-    out = {}
-    for k in args.kinds.split(","):
-        p = eap.params(k, prune=0, **KIND_PARAMS[k])
-        for _ in range(max(1, args.warmup)):
-            eap.eap_nn1(p, Q, R)
-        ms, cells = 0.0, 0
-        for _ in range(args.steps):
-            _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
-            ms += st["dp_ms"]
-            cells += st["cells_computed"]
-        # The algorithm's cells: for a windowed distance only those with
-        # |i - j| <= w (the kernel also touches some outside, masked to +inf).
-        L = ds.train.shape[1]
-        if "window_ratio" in KIND_PARAMS[k]:
-            w = int(math.floor(float(np.float32(KIND_PARAMS[k]["window_ratio"])) * L))
-            band = sum(min(L, i + w) - max(1, i - w) + 1 for i in range(1, L + 1))
-        else:
-            band = L * L
-        alg = band * ds.train.shape[0] * ds.test.shape[0] * args.steps
-        rate = alg / (ms / 1e3)
-        out[k] = {"dp_ms": ms / args.steps, "cells_per_s": rate, "ops_per_cell": OPS_PER_CELL[k],
-                  "alu_frac": rate * OPS_PER_CELL[k] / peak,
-                  "cells_roofline_per_s": peak / OPS_PER_CELL[k],
-                  "algorithmic_cells_per_pair": band,
-                  "computed_cells_per_pair": cells / (args.steps * ds.train.shape[0] * ds.test.shape[0])}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = unpruned_rows(eap, R, Q, ds.train.shape[1], args.kinds.split(","), args.steps, args.warmup, peak, flush)
     return {"metric": "unpruned (Base) DP algorithmic cell updates/s vs FP32 ALU roofline, 1000 x 1000 x 512",
             "value": out["dtw"]["cells_per_s"] if "dtw" in out else None, "unit": "cells/s",
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "base_dp_1000x1000_L512"}, "per_distance": out,
-            "roofline_peak_ops": peak}
+            "config": {"workload": "base_dp_1000x1000_L512", "l2": "flushed before each call (512 MiB write)"},
+            "per_distance": out, "roofline_peak_ops": peak}
 
 
 def workload_modes_512(args):
@@ -769,7 +890,11 @@ def run_other_workload(args):
     fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512, "subseq": workload_subseq,
           "allpairs_4096": workload_allpairs_4096,
           "uneven_64": workload_uneven_64, "serving": workload_serving}[args.workload]
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
     line = fn(args)
+    line["clocks"] = sampler.stop()
     line.setdefault("n_gpus", 1)
     print(json.dumps(line), flush=True)
     return 0

@@ -189,12 +189,18 @@ int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_
  * library and that every device loading libeap holds until the process
  * exits.  Nothing is allocated by the call: no cudaMalloc, cudaMallocAsync
  * or cudaFree.
- *   - Limit: the scratch must fit in 4 MiB.  ERP and the derivative
- *     variants each need 4 bytes per element of both sets; ERP, MSM and TWE
- *     also need 16 bytes per element of set a (+16) for their precomputed
- *     row constants; WDTW needs 128 KB.  (MSM: a->data_len up to about
- *     260,000; ERP: about 24 bytes per element of a plus 4 per element of b.)
- *     Larger requests return EAP_EINVAL without launching anything.
+ *   - Limit: the scratch must fit in 4 MiB (4,194,304 bytes).  With
+ *     na = a->data_len and nb = b->data_len, it is the sum of these pieces,
+ *     each rounded up to a multiple of 256 bytes:
+ *         8 + 64                        always (queue head, counters)
+ *         4*na + 4*nb                   ERP (border prefix sums)
+ *         4 * 32769                     WDTW (weight table, 131,076 bytes)
+ *         4*na + 4*nb                   any distance with derivative = 1
+ *         16*(na + 1)                   ERP, MSM, TWE (packed row constants)
+ *     So DTW and CDTW need 512 bytes at any size; MSM and TWE allow na up
+ *     to about 262,000; ERP needs 20*na + 4*nb (+ 4*na + 4*nb with the
+ *     derivative).  Larger requests return EAP_EINVAL without launching
+ *     anything.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
  *     stream capture.

@@ -8,7 +8,8 @@ arrays through ctypes.
 
 Functions mirror the plain definitions (see ``eap_oracle.c`` for citations):
 ``distance`` (Eq. Common + each distance's equations), ``eapruned``
-(Algorithm 5 with its cell counter), ``nn1`` (Algorithm 1), ``pairwise``
+(Algorithm 5 with its cell counter), ``nn1`` (Algorithm 1), ``nn1_eapruned``
+(Algorithm 1 calling Algorithm 5 with the best-so-far as cut-off), ``pairwise``
 (full matrix) and ``lb_keogh`` (textbook LB_Keogh).
 """
 from __future__ import annotations
@@ -91,6 +92,9 @@ def _load():
             lib.orc_nn1.restype = ctypes.c_int
             lib.orc_nn1.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int,
                                     f32p, i64p, i32p, ctypes.c_int, i32p, f64p, ctypes.c_int]
+            lib.orc_nn1_eapruned.restype = ctypes.c_int
+            lib.orc_nn1_eapruned.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int,
+                                             f32p, i64p, i32p, ctypes.c_int, i32p, f64p, i64p]
             lib.orc_pairwise.restype = ctypes.c_int
             lib.orc_pairwise.argtypes = [P(OrcParams), f32p, i64p, i32p, ctypes.c_int, f64p, ctypes.c_int]
             lib.orc_cross.restype = ctypes.c_int
@@ -171,6 +175,23 @@ def nn1(params: OrcParams, queries, refs, nthreads: int | None = None):
                     _ptr(rl, ctypes.c_int32), len(rl), _ptr(idx, ctypes.c_int32),
                     _ptr(dist, ctypes.c_double), int(nt))
     return idx, dist
+
+
+def nn1_eapruned(params: OrcParams, queries, refs):
+    """Algorithm 1 with Algorithm 5 as the distance (cut-off = best so far),
+    one thread, candidates in index order: (idx int32[nq], dist float64[nq],
+    computed cells)."""
+    qd, qo, ql = _packed_args(queries)
+    rd, ro, rl = _packed_args(refs)
+    nq = len(ql)
+    idx = np.zeros(nq, dtype=np.int32)
+    dist = np.zeros(nq, dtype=np.float64)
+    cells = ctypes.c_int64(0)
+    _load().orc_nn1_eapruned(ctypes.byref(params), _ptr(qd, ctypes.c_float), _ptr(qo, ctypes.c_int64),
+                             _ptr(ql, ctypes.c_int32), nq, _ptr(rd, ctypes.c_float), _ptr(ro, ctypes.c_int64),
+                             _ptr(rl, ctypes.c_int32), len(rl), _ptr(idx, ctypes.c_int32),
+                             _ptr(dist, ctypes.c_double), ctypes.byref(cells))
+    return idx, dist, int(cells.value)
 
 
 def pairwise(params: OrcParams, series, nthreads: int | None = None) -> np.ndarray:

@@ -23,6 +23,9 @@
  *                  abandoning on the row minimum), with a cell counter.
  *   orc_nn1        Algorithm 1 (NN search) over candidates in index order with
  *                  the strict "<" update; threads split the queries.
+ *   orc_nn1_eapruned  Algorithm 1 with Algorithm 5 as the distance and the
+ *                  best-so-far as its cut-off, single-threaded: the paper's
+ *                  own search (the like-for-like CPU baseline).
  *   orc_pairwise   the full distance matrix (the exact values that prune-only
  *                  mode must reproduce, Section 4 intro).
  *   orc_subseq     sub-sequence search (Section 5.3): every z-normalised
@@ -482,6 +485,35 @@ int orc_nn1(const orc_params* p,
     }
     for (int k = 0; k < nthreads; k++) pthread_join(th[k], NULL);
     free(th); free(jobs);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Algorithm 1 with Algorithm 5 as the distance, on one thread: the paper's
+ * own NN search.  Candidates are scanned in index order; each call gets the
+ * current d_nn as its cut-off (Section 2.2: the best-so-far is the cut-off)
+ * and a candidate replaces the best only when its result is strictly below
+ * it.  Returns the total number of computed cells in *cells.  An abandoned
+ * call returns +inf, which never wins, so the result is Algorithm 1's.
+ * ------------------------------------------------------------------------ */
+int orc_nn1_eapruned(const orc_params* p,
+                     const float* qd, const int64_t* qo, const int32_t* ql, int nq,
+                     const float* rd, const int64_t* ro, const int32_t* rl, int nr,
+                     int32_t* out_idx, double* out_dist, int64_t* cells) {
+    int64_t total = 0;
+    for (int q = 0; q < nq; q++) {
+        double dnn = OINF;
+        int32_t cnn = -1;
+        for (int c = 0; c < nr; c++) {
+            int64_t n = 0;
+            const double d = orc_eapruned(p, qd + qo[q], ql[q], rd + ro[c], rl[c], dnn, &n);
+            total += n;
+            if (d < dnn) { dnn = d; cnn = c; }
+        }
+        out_idx[q] = cnn;
+        out_dist[q] = dnn;
+    }
+    if (cells) *cells = total;
     return 0;
 }
 

@@ -1224,7 +1224,11 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.kind = p->kind;
     c.cost = cost;
     c.prune = p->prune;
+    // The same mapping as eap_pairs: CTA per pair for long unwindowed series
+    // (the autotuned map or the default), else warp groups or band.
+    c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
+    if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g);
     c.sms = sms;
     c.max_rows = ma;

@@ -284,6 +284,31 @@ def test_nn1_and_pairwise_match_distance():
             assert M[i, j] == O.distance(p, tr.series(i), tr.series(j))
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_nn1_eapruned_equals_plain_nn1(kind):
+    # The paper's exactness claim (Section 5): every implementation of a
+    # distance gives the same NN result.  Alg. 1 driving Alg. 5 with the
+    # best-so-far as cut-off must return the plain search's index (lowest on
+    # ties) and distance, bit for bit in FP64, while computing fewer cells
+    # than the full matrices.  Ragged lengths, and exact duplicates of the
+    # query among the candidates, exercise the tie and the zero-distance case.
+    rng = np.random.default_rng(31 + KINDS.index(kind))
+    refs = [synth.random_walks(rng, 1, int(n))[0].astype(np.float32) for n in rng.integers(18, 30, size=14)]
+    qs = [synth.random_walks(rng, 1, int(n))[0].astype(np.float32) for n in rng.integers(18, 30, size=5)]
+    refs[9] = qs[2].copy()
+    refs[11] = qs[2].copy()
+    kw = {"window_ratio": 0.3} if kind in ("cdtw", "erp") else {}
+    p = O.make_params(kind, **kw)
+    tr, te = synth.pack(refs), synth.pack(qs)
+    idx, dist = O.nn1(p, te, tr, nthreads=1)
+    idx2, dist2, cells = O.nn1_eapruned(p, te, tr)
+    assert list(idx2) == list(idx)
+    assert list(dist2) == list(dist)
+    assert idx[2] == 9 and dist[2] == 0.0
+    full = sum(len(q) * len(r) for q in qs for r in refs)
+    assert 0 < cells < full
+
+
 def test_nn1_ties_go_to_lowest_index_and_empty_is_minus_one():
     p = O.make_params("dtw")
     q = synth.pack([np.array([0.0, 1.0, 2.0], np.float32)])
