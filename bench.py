@@ -54,10 +54,10 @@ N_TRAIN, N_TEST, LENGTH, N_CLASSES = 1000, 1000, 512, 10
 # the library build whose source fingerprint is recorded with it.
 # The EAPruned DP launch of this workload (L = 512) per distance: 16 lanes per
 # pair over column panels (W = 5, WDTW 4), CDTW and ERP in band coordinates
-# (CDTW 8 lanes x 14 cells per row, ERP 16 x 7).
+# (8 lanes x 13 cells = the 2w + 2 = 104 positions of a band row).
 DP_KERNELS = {"dtw": "group_dp_kernel<dtw, W=5, G=16>", "wdtw": "group_dp_kernel<wdtw, W=4, G=16>",
               "msm": "group_dp_kernel<msm, W=5, G=16>", "twe": "group_dp_kernel<twe, W=5, G=16>",
-              "cdtw": "band_dp_kernel<cdtw, W=14, G=8>", "erp": "band_dp_kernel<erp, W=7, G=16>"}
+              "cdtw": "band_dp_kernel<cdtw, W=13, G=8, exact>", "erp": "band_dp_kernel<erp, W=13, G=8, exact>"}
 TRAFFIC = {"kernel": "group_dp_kernel<msm, W=5, G=16>", "bytes": 14904832,
            "fingerprint": "b97c62c72a4c5d36dfe0f665d20f7ccdaedd9d58e861bf74da3b874fd9e27d52"}
 METRIC = "1-NN queries/s (six distances, EAPruned, 1000 train x 1000 test, L=512)"

@@ -440,16 +440,20 @@ int choose_group(int kind, int cost, int max_rows, int max_cols, int prune, int 
 
 // Band mapping (band_dp_kernel) for the DP of CDTW and ERP in every mode
 // (Base; EAPruned and EABase abandon on the band's cut, and the lanes compute
-// whole band rows either way): a row of the window, plus the two border cells
-// it reaches, is 2w + 3 cells, and the narrowest built launch that holds the
-// widest pair's band is taken.  A launch is sized for the widest band, so it
-// is used only where every pair fills at least half of it and every series
-// is at least as long as the widest band (else the column-panel kernels do
-// less work).  EAP_BAND=0 turns it off, EAP_BAND=2 takes it whenever the band
-// fits a launch (tests).
-void choose_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G) {
+// whole band rows either way).  A row of the window plus the cell left of it
+// is 2w + 2 positions.  When every pair of the call has the same window and
+// a built launch holds exactly 2w + 2 positions, that exact launch is taken
+// (no addend right of the window); otherwise the narrowest built launch with
+// at least 2w + 3 positions for the widest pair.  A launch is sized for the
+// widest band, so it is used only where every pair fills at least half of it
+// and every series is at least as long as the widest band (else the
+// column-panel kernels do less work).  EAP_BAND=0 turns it off, EAP_BAND=2
+// takes it whenever the band fits a launch (tests); EAP_BAND_EXACT=0 skips
+// the exact launches; EAP_BAND_G = 4, 8 or 16 restricts the lanes per pair.
+void choose_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G, int* exact) {
     *W = 0;
     *G = 0;
+    *exact = 0;
     if (kind != EAP_CDTW && kind != EAP_ERP) return;
     if (prune != kPmBase && prune != kPmPruned && prune != kPmEA) return;
     const char* e = std::getenv("EAP_BAND");
@@ -462,16 +466,33 @@ void choose_band(int kind, int prune, const KParams& kp, int min_len, int max_le
     };
     const long long w_hi = window(max_len), w_lo = window(min_len);
     if (w_hi < 0) return;
-    const long long B = 2 * w_hi + 3;
-    static const int kBands8[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};     // (W, G)
-    static const int kBands16[][2] = {{4, 8}, {4, 16}, {7, 16}, {8, 16}, {16, 16}};
-    // 8 lanes per pair except for the abandoning ERP DP, whose wider cells
-    // need fewer per lane to keep registers and occupancy up (1000 x 1000 x
-    // 512, w = 51: ERP 11.0 -> 9.5 ms with 16 lanes x 7; CDTW and the Base DP
-    // are faster with 8 lanes).  EAP_BAND_G = 8 or 16 overrides.
     const char* g = std::getenv("EAP_BAND_G");
-    const int gsel = g ? std::atoi(g) : ((kind == EAP_ERP && prune != kPmBase) ? 16 : 8);
-    for (const auto& b : (gsel == 16 ? kBands16 : kBands8)) {
+    const int gsel = g ? std::atoi(g) : 0;
+    const char* ex = std::getenv("EAP_BAND_EXACT");
+    const bool try_exact = !(ex && ex[0] == '0');
+    // Exact launches (W, G): 8 lanes x 13 and 4 lanes x 26 hold 104 = 2w + 2
+    // positions (w = 51).  8 lanes first (measured on 1000 x 1000 x 512).
+    static const int kExact[][2] = {{13, 8}, {26, 4}};
+    if (try_exact && w_lo == w_hi && (mode == 2 || 2 * w_hi + 2 <= min_len)) {
+        for (const auto& b : kExact) {
+            if (gsel && gsel != b[1]) continue;
+            if ((long long)b[0] * b[1] != 2 * w_hi + 2) continue;
+            *W = b[0];
+            *G = b[1];
+            *exact = 1;
+            return;
+        }
+    }
+    const long long B = 2 * w_hi + 3;
+    static const int kBands8[][2] = {{4, 8}, {8, 8}, {14, 8}, {16, 8}, {16, 16}};     // (W, G), padded
+    static const int kBands16[][2] = {{4, 8}, {7, 16}, {16, 16}};
+    // 8 lanes per pair except for the abandoning ERP DP, whose wider cells
+    // need fewer per lane to keep registers and occupancy up.
+    const int gpref = gsel ? gsel : ((kind == EAP_ERP && prune != kPmBase) ? 16 : 8);
+    const int (*bands)[2] = gpref == 16 ? kBands16 : kBands8;
+    const int nb = gpref == 16 ? (int)(sizeof(kBands16) / sizeof(kBands16[0])) : (int)(sizeof(kBands8) / sizeof(kBands8[0]));
+    for (int k = 0; k < nb; ++k) {
+        const int* b = bands[k];
         const long long P = (long long)b[0] * b[1];
         if (P < B) continue;
         if (mode != 2 && (B > min_len || P > 2 * (2 * w_lo + 3))) return;
@@ -707,7 +728,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
     choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mr, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g, &c.band_exact);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -964,7 +985,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.max_cols = mx;
         c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
         c.group = c.cta ? 0 : choose_group(p->kind, cost, mx, mx, c.prune, c.W);
-        choose_band(p->kind, c.prune, c.kp, set_min_len(set), mx, &c.band, &c.band_g);
+        choose_band(p->kind, c.prune, c.kp, set_min_len(set), mx, &c.band, &c.band_g, &c.band_exact);
         c.stream = st;
         c.ub = L.ub;
         if (prune && (e = dispatch(c, true))) { sc.release(); return cuda_status(e); }
@@ -1057,7 +1078,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g, &c.band_exact);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
     tm.start(st);
@@ -1229,7 +1250,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g);
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g, &c.band_exact);
     c.sms = sms;
     c.max_rows = ma;
     c.max_cols = mb;
@@ -1287,8 +1308,8 @@ int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     return choose_group(kind, cost, max_rows, max_cols, prune, W);
 }
-void pick_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G) {
-    choose_band(kind, prune, kp, min_len, max_len, W, G);
+void pick_band(int kind, int prune, const KParams& kp, int min_len, int max_len, int* W, int* G, int* exact) {
+    choose_band(kind, prune, kp, min_len, max_len, W, G, exact);
 }
 
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G) {

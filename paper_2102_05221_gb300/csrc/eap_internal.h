@@ -26,6 +26,7 @@ struct LaunchCtx {
     int cta;             // 1: CTA-per-pair mapping (long, unwindowed series); 0: warp per pair
     int band = 0;        // windowed DP in band coordinates (Base, EAPruned): strip width (0 = not used)
     int band_g = 0;      // lanes per pair of the band mapping
+    int band_exact = 0;  // 1: the launch holds exactly 2w + 2 band positions (no right-of-window addend)
     cudaStream_t stream;
     float* ub;           // diagonal-path upper bounds (output of launch_ub)
 };
@@ -56,7 +57,7 @@ int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W)
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G);
 // Band mapping of the windowed DP: strip width and lanes per pair, or 0
 // (min_len / max_len: shortest and longest series of the call).
-void pick_band(int kind, int prune, const eapd::KParams& kp, int min_len, int max_len, int* W, int* G);
+void pick_band(int kind, int prune, const eapd::KParams& kp, int min_len, int max_len, int* W, int* G, int* exact);
 int bucket_of(int len);
 
 // Pre-pass launches shared with the batched path (eap_api.cu).
@@ -111,11 +112,11 @@ int run_dp(const LaunchCtx& c) {
 // DP of a windowed distance in band coordinates (band_dp_kernel): Base, or
 // early abandoning for EAPruned and EABase (every cell of a row is computed
 // either way), G lanes per pair.
-template <class F, int W, int G>
+template <class F, int W, int G, bool EXACT>
 int run_band(const LaunchCtx& c) {
     using namespace eapd;
     void (*kern)(const DPJob, const KParams) =
-        c.prune == kPmBase ? band_dp_kernel<F, W, G, kPmBase> : band_dp_kernel<F, W, G, kPmPruned>;
+        c.prune == kPmBase ? band_dp_kernel<F, W, G, kPmBase, EXACT> : band_dp_kernel<F, W, G, kPmPruned, EXACT>;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     if (e != cudaSuccess) return (int)e;
@@ -223,16 +224,17 @@ int run_kind(const LaunchCtx& c, bool ub_only) {
         if (c.cta) return c.W >= 8 ? run_cta<F, 8>(d) : run_cta<F, 4>(d);
     } else {
         if (c.band) {
-            if (c.band_g == 8) {
-                if (c.band == 4) return run_band<F, 4, 8>(d);
-                if (c.band == 8) return run_band<F, 8, 8>(d);
-                if (c.band == 14) return run_band<F, 14, 8>(d);
-                if (c.band == 16) return run_band<F, 16, 8>(d);
+            if (c.band_exact) {
+                if (c.band_g == 8 && c.band == 13) return run_band<F, 13, 8, true>(d);
+                if (c.band_g == 4 && c.band == 26) return run_band<F, 26, 4, true>(d);
+            } else if (c.band_g == 8) {
+                if (c.band == 4) return run_band<F, 4, 8, false>(d);
+                if (c.band == 8) return run_band<F, 8, 8, false>(d);
+                if (c.band == 14) return run_band<F, 14, 8, false>(d);
+                if (c.band == 16) return run_band<F, 16, 8, false>(d);
             } else if (c.band_g == 16) {
-                if (c.band == 4) return run_band<F, 4, 16>(d);
-                if (c.band == 7) return run_band<F, 7, 16>(d);
-                if (c.band == 8) return run_band<F, 8, 16>(d);
-                if (c.band == 16) return run_band<F, 16, 16>(d);
+                if (c.band == 7) return run_band<F, 7, 16, false>(d);
+                if (c.band == 16) return run_band<F, 16, 16, false>(d);
             }
             return (int)cudaErrorInvalidValue;
         }

@@ -16,8 +16,10 @@ from tests.parity_util import close, check_nn, gpu_params, oracle_params
 
 pytestmark = pytest.mark.gpu
 
-# Band rows hold 2w + 3 cells; the built launches hold 32, 64, 112, 128, 256.
-BAND_WINDOWS = [0, 1, 2, 14, 15, 30, 31, 54, 55, 62, 63, 126, 127]
+# A band row is 2w + 2 positions (the window and the cell left of it).  The
+# padded launches hold 32, 64, 112, 128 and 256 positions and need 2w + 3;
+# the exact launches hold 2w + 2 = 104 (w = 51: 8 lanes x 13, 4 lanes x 26).
+BAND_WINDOWS = [0, 1, 2, 14, 15, 30, 31, 50, 51, 54, 55, 62, 63, 126, 127]
 
 
 @pytest.fixture(scope="module")
@@ -27,18 +29,21 @@ def eap():
     return E
 
 
-def _run(fn, band):
+def _run(fn, band, **env):
     """Runs fn with the band mapping forced (EAP_BAND=2: whenever the band
-    fits a launch, even where the default keeps the panel kernels) or off."""
-    old = os.environ.get("EAP_BAND")
-    os.environ["EAP_BAND"] = "2" if band else "0"
+    fits a launch, even where the default keeps the panel kernels) or off,
+    and any other EAP_* variables given (EAP_BAND_G, EAP_BAND_EXACT)."""
+    env = dict(env, EAP_BAND="2" if band else "0")
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: str(v) for k, v in env.items()})
     try:
         return fn()
     finally:
-        if old is None:
-            os.environ.pop("EAP_BAND", None)
-        else:
-            os.environ["EAP_BAND"] = old
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("kind", ["cdtw", "erp"])
@@ -103,15 +108,16 @@ def test_band_pairwise_base_matches_panels(eap, kind):
 
 
 def test_band_cells_and_workload_sample(eap):
-    """1000 x 1000 x 512 CDTW (w = 51): one band row of 112 cells per series
-    row, and sampled 1-NN equal to the oracle."""
+    """1000 x 1000 x 512 CDTW (w = 51, the exact 8 x 13 launch): 2w + 1 = 103
+    window positions counted per series row, and sampled 1-NN equal to the
+    oracle."""
     ds = synth.workload_nn1_512()
     tr, te = synth.pack(ds.train), synth.pack(ds.test)
     R, Q = eap.SeriesSet.from_packed(tr), eap.SeriesSet.from_packed(te)
     p = gpu_params(eap, "cdtw", prune=0, window_ratio=0.1)
     idx, dist, st = eap.eap_nn1(p, Q, R, with_stats=True)
     assert st["pairs"] == 1000 * 1000
-    assert st["cells_computed"] == 1000 * 1000 * 512 * 112
+    assert st["cells_computed"] == 1000 * 1000 * 512 * 103
     rows = list(np.random.default_rng(11).choice(1000, size=6, replace=False))
     D = O.cross(oracle_params("cdtw", window_ratio=0.1), synth.pack([ds.test[r] for r in rows]), tr)
     check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D, rows=rows)
@@ -211,3 +217,44 @@ def test_band_default_choice(eap):
     _, st = eap.eap_pairs(p, A, A, ia, ib, with_stats=True)
     L = np.asarray(lens, dtype=np.int64)
     assert st["cells_computed"] <= int((L[ia] * L[ib]).sum())
+
+
+@pytest.mark.parametrize("kind", ["cdtw", "erp"])
+@pytest.mark.parametrize("cost", [0, 1])
+@pytest.mark.parametrize("launch", [{"EAP_BAND_G": 8}, {"EAP_BAND_G": 4}, {"EAP_BAND_EXACT": 0}])
+def test_band_exact_launches_match_panels_and_oracle(eap, kind, cost, launch):
+    """w = 51: the exact launches (8 lanes x 13, 4 lanes x 26 positions, no
+    addend right of the window; ERP's top border cell M(0, w + 1) enters the
+    last lane in row 1) and the padded launch, Base and EAPruned, against the
+    column-panel kernels (bit for bit) and the oracle."""
+    w = 51
+    la = [104, 104, 130, 155, 104 + w, 120, 200, 104]
+    lb = [104, 104 + w, 104, 140, 104, 171, 200, 150]
+    Ap = synth.ragged_walks(len(la), la, 5100 + cost, n_classes=2)
+    Bp = synth.ragged_walks(len(lb), lb, 5101 + cost, n_classes=2)
+    A, B = eap.SeriesSet.from_packed(Ap), eap.SeriesSet.from_packed(Bp)
+    kw = {"window": w, "cost": cost}
+    if kind == "erp":
+        kw["erp_gap"] = 0.25
+    ia = np.repeat(np.arange(len(la)), len(lb)).astype(np.int32)
+    ib = np.tile(np.arange(len(lb)), len(la)).astype(np.int32)
+    p0 = gpu_params(eap, kind, prune=0, **kw)
+    got, st = _run(lambda: eap.eap_pairs(p0, A, B, ia, ib, with_stats=True), True, **launch)
+    ref = _run(lambda: eap.eap_pairs(p0, A, B, ia, ib), False)
+    got, ref = got.cpu().numpy(), ref.cpu().numpy()
+    assert np.array_equal(got, ref), (kind, cost, launch, np.flatnonzero(got != ref)[:5])
+    D = O.cross(oracle_params(kind, **kw), Ap, Bp)
+    for k in range(len(ia)):
+        d = float(D[ia[k], ib[k]])
+        assert np.isinf(got[k]) if np.isinf(d) else close(float(got[k]), d), (kind, cost, launch, k)
+    # Counted cells: every row of a feasible pair holds the 2w + 1 window
+    # positions; a pair with |L_A - L_B| > w is decided before any row.
+    feas = [k for k in range(len(ia)) if abs(la[ia[k]] - lb[ib[k]]) <= w]
+    assert st["cells_computed"] == sum(la[ia[k]] for k in feas) * (2 * w + 1)
+    p1 = gpu_params(eap, kind, prune=1, **kw)
+    fin = np.isfinite(got)
+    for scale in (0.5, 1.0, 1.5):
+        cut = np.where(fin, got * np.float32(scale), np.float32(1.0)).astype(np.float32)
+        g1 = _run(lambda: eap.eap_pairs(p1, A, B, ia, ib, cut), True, **launch).cpu().numpy()
+        want = np.where(fin & (got <= cut), got, np.float32(np.inf))
+        assert np.array_equal(g1, want), (kind, cost, launch, scale)
