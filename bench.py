@@ -300,7 +300,7 @@ def main():
                     help="per-distance: one eap_nn1 call per distance; batch: all six in one eap_nn1_batch launch")
     ap.add_argument("--workload", default="nn1_512",
                     choices=["nn1_512", "unpruned_512", "modes_512", "subseq", "allpairs_4096", "uneven_64",
-                             "serving"],
+                             "serving", "lb_cascade"],
                     help="nn1_512 is the benchmark; the others measure the remaining workloads")
     args = ap.parse_args()
     kinds = [k for k in args.kinds.split(",") if k]
@@ -611,6 +611,52 @@ def workload_unpruned_512(args):
             "per_distance": out, "roofline_peak_ops": peak}
 
 
+def workload_lb_cascade(args):
+    """The envelope + LB_Keogh pass (Alg. 2, the lb-keogh2 cascade of Section
+    5.2) ahead of the EAPruned CDTW DP: 64 queries against 40,000 candidates
+    of length 512 (z-normalised random walks; candidates and their envelopes
+    take 246 MB, more than the 129 MB L2).  The pass is timed by the library
+    with CUDA events on the launching stream (stats lb_ms); its HBM roofline
+    counts the bytes it must move: every series read once, every envelope
+    written once and read once, the bound matrix written once."""
+    import numpy as np
+    import torch
+
+    from paper_2102_05221_gb300 import eap, synth
+    nq, nr, L = 64, 40000, 512
+    rng = np.random.default_rng(5120)
+    R = eap.SeriesSet.from_matrix(synth.random_walks(rng, nr, L).astype(np.float32))
+    Q = eap.SeriesSet.from_matrix(synth.random_walks(rng, nq, L).astype(np.float32))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    p = eap.params("cdtw", window_ratio=0.1, lb=2)
+    for _ in range(max(1, args.warmup)):
+        eap.eap_nn1(p, Q, R)
+    lb_ms, dp_ms, pruned, pairs = [], [], 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
+        lb_ms.append(st["lb_ms"])
+        dp_ms.append(st["dp_ms"])
+        pruned += st["pairs_lb_pruned"]
+        pairs += st["pairs"]
+    t = statistics.median(lb_ms)
+    elems = (nq + nr) * L
+    unique = elems * 4 + elems * 8 + elems * 8 + nq * nr * 4   # series read, envelopes written + read, bounds written
+    per_pair = nq * nr * L * 12                                # 4 B + 8 B (reverse) per element per pair, no reuse
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    return {"metric": "envelope + LB_Keogh2 pass GB/s (64 x 40,000 x 512, CDTW 10%) vs HBM",
+            "value": unique / (t / 1e3) / 1e9, "unit": "GB/s", "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "lb_keogh2_64x40000_L512", "l2": "flushed before each call (512 MiB write); "
+                       "candidates + envelopes 246 MB > L2"},
+            "lb_ms": t, "dp_ms": statistics.median(dp_ms), "pairs_lb_pruned_frac": pruned / max(1, pairs),
+            "roofline": {"bound": "hbm", "achieved": unique / (t / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": unique / (t / 1e3) / 1e9 / peak, "traffic": None,
+                         "basis": "unique bytes: series 4 B/elem read, envelopes 8 B/elem written and read, "
+                                  "bounds 4 B/pair written"},
+            "algorithmic_per_pair_gbs": per_pair / (t / 1e3) / 1e9}
+
+
 def workload_modes_512(args):
     """Base, Prune, EABase and EAPruned 1-NN (the four implementations of the
     paper's NN experiment, Section 5.1) on the 1000 x 1000 x 512 workload:
@@ -889,7 +935,7 @@ def run_other_workload(args):
     eap.load()
     fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512, "subseq": workload_subseq,
           "allpairs_4096": workload_allpairs_4096,
-          "uneven_64": workload_uneven_64, "serving": workload_serving}[args.workload]
+          "uneven_64": workload_uneven_64, "serving": workload_serving, "lb_cascade": workload_lb_cascade}[args.workload]
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)

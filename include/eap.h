@@ -116,6 +116,8 @@ typedef struct {
     uint64_t cells_effective;  /* sum over all pairs of L_S * L_T */
     uint64_t cells_computed;   /* cells the DP kernels evaluated (after pruning) */
     double   dp_ms;            /* device time of the DP kernel launch(es), CUDA events on the call's stream */
+    double   lb_ms;            /* device time of the envelope + LB_Keogh launches (eap_nn1 with a lower
+                                * bound), CUDA events on the call's stream; 0 otherwise */
 } eap_stats;
 
 /* Inputs must be finite.  Validation mode -- the environment variable
@@ -147,6 +149,29 @@ int eap_nn1_host(const eap_params* p,
                  const float* q_data, const int64_t* q_offsets, const int32_t* q_lengths, int32_t nq,
                  const float* r_data, const int64_t* r_offsets, const int32_t* r_lengths, int32_t nr,
                  int32_t* out_idx, float* out_dist, eap_stats* opt_stats);
+
+/* 1-NN against one shard of the candidates, as packed keys for the one
+ * exchange step of candidate sharding (Alg. 1 over the union of the shards
+ * is the per-query minimum of the shards' keys).  Same search as eap_nn1;
+ * instead of (index, distance) it writes, per query,
+ *     out_keys[q] = (float bits of D) << 32 | (local index + index_offset)
+ * or (+inf bits) << 32 | 0xffffffff when no candidate of the shard is
+ * finite.  Distances are >= 0, so the keys order like (distance, global
+ * index) both as unsigned and as signed 64-bit integers: an element-wise MIN
+ * over the shards (e.g. an all-reduce) keeps the smallest distance and, among
+ * equal ones, the lowest global index -- Alg. 1's strict "<" over the
+ * candidates in index order.
+ *   out_keys      device uint64[queries->count]
+ *   index_offset  global index of refs' first series; index_offset >= 0 and
+ *                 index_offset + refs->count < 2^32 - 1, else EAP_EINVAL.
+ * Asynchronous on the stream like eap_nn1. */
+int eap_nn1_keys(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs,
+                 int64_t index_offset, uint64_t* out_keys, void* cuda_stream, eap_stats* opt_stats);
+
+/* Keys of eap_nn1_keys (after the min-reduction) to results:
+ * out_idx[q] = the key's index, or -1 for "none"; out_dist[q] = D, or +inf.
+ * keys, out_idx, out_dist: device arrays of n elements. */
+int eap_keys_unpack(const uint64_t* keys, int32_t n, int32_t* out_idx, float* out_dist, void* cuda_stream);
 
 #define EAP_PRUNE_ONLY 0   /* EAPruned with each pair's own diagonal-path cost as cut-off: exact, prunes but never abandons (Section 4 intro) */
 #define EAP_BASE       1   /* plain Base DP (Alg. 3) */

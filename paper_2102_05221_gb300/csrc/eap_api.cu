@@ -90,6 +90,35 @@ __global__ void unpack_kernel(const unsigned long long* __restrict__ best, int n
     }
 }
 
+// Per-query result as a packed key for a min-reduction across candidate
+// shards: (distance bits << 32) | (index + offset), or (+inf bits << 32) |
+// 0xffffffff when no candidate of the shard is finite.  Distances are >= 0,
+// so the keys order like (distance, index) -- Alg. 1's strict "<" over
+// candidates in index order -- as unsigned and as signed 64-bit integers.
+__global__ void keys_kernel(const unsigned long long* __restrict__ best, int n, long long offset,
+                            unsigned long long* __restrict__ keys, unsigned long long* stats) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long b = best ? best[i] : pack_best(EAP_FINF, kNoIndex);   // null: an empty shard
+        const unsigned ix = (unsigned)(b & 0xffffffffu);
+        if (ix == kNoIndex) {
+            if (__uint_as_float((unsigned)(b >> 32)) != EAP_FINF && stats) atomicAdd(stats + kStatErrors, 1ULL);
+            keys[i] = pack_best(EAP_FINF, kNoIndex);
+        } else {
+            keys[i] = (b & 0xffffffff00000000ULL) | (unsigned long long)((long long)ix + offset);
+        }
+    }
+}
+
+__global__ void keys_unpack_kernel(const unsigned long long* __restrict__ keys, int n, int32_t* __restrict__ idx,
+                                   float* __restrict__ dist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        const unsigned ix = (unsigned)(k & 0xffffffffu);
+        idx[i] = ix == kNoIndex ? -1 : (int32_t)ix;
+        dist[i] = ix == kNoIndex ? EAP_FINF : __uint_as_float((unsigned)(k >> 32));
+    }
+}
+
 // ERP borders (Eq. ERP): border[off + k] = sum_{m <= k+1} cost(x_m, g), in order.
 __global__ void erp_border_kernel(const float* __restrict__ data, const int64_t* __restrict__ off,
                                   const int32_t* __restrict__ len, int n, float g, int cost,
@@ -213,44 +242,134 @@ __global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict
 // Lower bound of every (query, candidate) pair, [q][c]: LB_Keogh(Q, C) (the
 // query's envelope bounds C), and with two_way also LB_Keogh(C, Q); the
 // larger one is kept (the lb-keogh2 cascade of Section 5.2 in one pass).
-// Pairs of unequal length get 0.  The bound is shrunk by `shrink` so float
-// rounding can never lift it above the float32 DP value of the pair.
-__global__ void lb_matrix_kernel(const SeriesDev Q, const SeriesDev R, const float* __restrict__ qU,
-                                 const float* __restrict__ qL, const float* __restrict__ rU,
-                                 const float* __restrict__ rL, int cost, int two_way, float* __restrict__ lb) {
-    const int q = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int Lq = Q.len[q];
-    const int64_t oq = Q.off[q];
-    const float* x = Q.data + oq;
-    const float shrink = 1.0f - (float)(4 * Lq + 16) * 5.9604645e-8f;   // 1 - (4L + 16) 2^-24
-    for (int c = warp; c < R.n; c += nw) {
-        float acc1 = 0.f, acc2 = 0.f;
-        if (R.len[c] == Lq) {
-            const int64_t oc = R.off[c];
-            const float* y = R.data + oc;
-            for (int i = lane; i < Lq; i += 32) {
-                const float yi = __ldg(y + i), u = __ldg(qU + oq + i), lo = __ldg(qL + oq + i);
-                float e = 0.f;
-                if (yi > u) e = cost == 0 ? pcost<0>(yi, u) : pcost<1>(yi, u);
-                else if (yi < lo) e = cost == 0 ? pcost<0>(yi, lo) : pcost<1>(yi, lo);
-                acc1 = __fadd_rn(acc1, e);
+// Pairs of unequal length get 0.  The bound is shrunk by 1 - (4L + 16) 2^-24
+// so float rounding can never lift it above the float32 DP value of the pair.
+//
+// Tiled like a matrix product: a block owns kLbTq queries x kLbTc candidates
+// and walks the points in chunks of kLbK, staging the chunk of every series
+// of the tile (query: U, L, x; candidate: y, U, L) in shared memory once, so
+// each candidate chunk is read from memory once per query tile instead of
+// once per query.  Thread (ty, tx) of the 16 x 16 block accumulates the 4 x 4
+// pairs (ty + 16a, tx + 16b).  Per point and direction, the textbook case
+// split "cost(c_i, U_i) if c_i > U_i, cost(c_i, L_i) if c_i < L_i, else 0" is
+// cost(c_i, clamp(c_i, L_i, U_i)): the same difference, rounded the same way.
+// Points past a series' end are padded so that they add 0.
+constexpr int kLbTq = 64, kLbTc = 64, kLbK = 32;
+constexpr int kLbStride = kLbK + 1;   // shared-memory row pitch (conflict-free column reads)
+constexpr size_t kLbSmemBytes = sizeof(float) * 6 * 64 * kLbStride;
+
+__device__ __forceinline__ float lb_term(float y, float lo, float up, int cost, float acc) {
+    const float d = __fsub_rn(y, fminf(fmaxf(y, lo), up));
+    return cost == 0 ? __fmaf_rn(d, d, acc) : __fadd_rn(acc, fabsf(d));
+}
+
+__global__ void __launch_bounds__(256) lb_matrix_kernel(const SeriesDev Q, const SeriesDev R,
+                                                        const float* __restrict__ qU, const float* __restrict__ qL,
+                                                        const float* __restrict__ rU, const float* __restrict__ rL,
+                                                        int cost, int two_way, float* __restrict__ lb) {
+    extern __shared__ float lbs[];
+    float* sqU = lbs;                          // [64][kLbStride] per array
+    float* sqL = sqU + 64 * kLbStride;
+    float* sqx = sqL + 64 * kLbStride;
+    float* scy = sqx + 64 * kLbStride;
+    float* scU = scy + 64 * kLbStride;
+    float* scL = scU + 64 * kLbStride;
+    __shared__ int s_len[kLbTq + kLbTc];
+    __shared__ int64_t s_off[kLbTq + kLbTc];
+    __shared__ int s_max;
+    const int q0 = blockIdx.y * kLbTq, c0 = blockIdx.x * kLbTc;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    if (threadIdx.x < kLbTq + kLbTc) {
+        const int k = threadIdx.x;
+        int len = 0;
+        int64_t off = 0;
+        if (k < kLbTq) {
+            if (q0 + k < Q.n) { len = Q.len[q0 + k]; off = Q.off[q0 + k]; }
+        } else if (c0 + k - kLbTq < R.n) {
+            len = R.len[c0 + k - kLbTq];
+            off = R.off[c0 + k - kLbTq];
+        }
+        s_len[k] = len;
+        s_off[k] = off;
+        atomicMax(&s_max, len);
+    }
+    __syncthreads();
+    const int maxlen = s_max;
+    float acc1[4][4], acc2[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) { acc1[a][b] = 0.f; acc2[a][b] = 0.f; }
+    for (int i0 = 0; i0 < maxlen; i0 += kLbK) {
+        // Stage the chunk: 128 series x 32 points, one warp per series row at a time.
+        for (int r = threadIdx.x >> 5; r < kLbTq + kLbTc; r += 8) {
+            const int i = i0 + (threadIdx.x & 31);
+            const bool in = i < s_len[r];
+            const int64_t o = s_off[r] + i;
+            const int col = threadIdx.x & 31;
+            if (r < kLbTq) {
+                sqU[r * kLbStride + col] = in ? __ldg(qU + o) : EAP_FINF;
+                sqL[r * kLbStride + col] = in ? __ldg(qL + o) : -EAP_FINF;
+                if (two_way) sqx[r * kLbStride + col] = in ? __ldg(Q.data + o) : 0.f;
+            } else {
+                const int rc = r - kLbTq;
+                scy[rc * kLbStride + col] = in ? __ldg(R.data + o) : 0.f;
                 if (two_way) {
-                    const float xi = __ldg(x + i), u2 = __ldg(rU + oc + i), l2 = __ldg(rL + oc + i);
-                    float e2 = 0.f;
-                    if (xi > u2) e2 = cost == 0 ? pcost<0>(xi, u2) : pcost<1>(xi, u2);
-                    else if (xi < l2) e2 = cost == 0 ? pcost<0>(xi, l2) : pcost<1>(xi, l2);
-                    acc2 = __fadd_rn(acc2, e2);
+                    scU[rc * kLbStride + col] = in ? __ldg(rU + o) : EAP_FINF;
+                    scL[rc * kLbStride + col] = in ? __ldg(rL + o) : -EAP_FINF;
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                acc1 = __fadd_rn(acc1, __shfl_xor_sync(EAP_FULL, acc1, o));
-                acc2 = __fadd_rn(acc2, __shfl_xor_sync(EAP_FULL, acc2, o));
-            }
         }
-        if (lane == 0) lb[(size_t)q * R.n + c] = __fmul_rn(fmaxf(acc1, acc2), shrink);
+        __syncthreads();
+        const int kend = min(kLbK, maxlen - i0);
+        for (int k = 0; k < kend; ++k) {
+            float u[4], l[4], x[4], y[4], cu[4], cl[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                u[a] = sqU[(ty + 16 * a) * kLbStride + k];
+                l[a] = sqL[(ty + 16 * a) * kLbStride + k];
+                if (two_way) x[a] = sqx[(ty + 16 * a) * kLbStride + k];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                y[b] = scy[(tx + 16 * b) * kLbStride + k];
+                if (two_way) { cu[b] = scU[(tx + 16 * b) * kLbStride + k]; cl[b] = scL[(tx + 16 * b) * kLbStride + k]; }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc1[a][b] = lb_term(y[b], l[a], u[a], cost, acc1[a][b]);
+                    if (two_way) acc2[a][b] = lb_term(x[a], cl[b], cu[b], cost, acc2[a][b]);
+                }
+        }
+        __syncthreads();
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int qa = ty + 16 * a, q = q0 + qa;
+        if (q >= Q.n) continue;
+        const int Lq = s_len[qa];
+        const float shrink = 1.0f - (float)(4 * Lq + 16) * 5.9604645e-8f;   // 1 - (4L + 16) 2^-24
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int cb = tx + 16 * b, c = c0 + cb;
+            if (c >= R.n) continue;
+            const float v = s_len[kLbTq + cb] == Lq ? __fmul_rn(fmaxf(acc1[a][b], acc2[a][b]), shrink) : 0.f;
+            lb[(size_t)q * R.n + c] = v;
+        }
+    }
+}
+
+void launch_lb_matrix(const SeriesDev& Q, const SeriesDev& R, const float* qU, const float* qL, const float* rU,
+                      const float* rL, int cost, int two_way, float* lb, cudaStream_t st) {
+    if (Q.n <= 0 || R.n <= 0) return;
+    // Opt-in shared memory above 48 KB (a property of the kernel on the current device).
+    cudaFuncSetAttribute(lb_matrix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLbSmemBytes);
+    const dim3 grid((unsigned)((R.n + kLbTc - 1) / kLbTc), (unsigned)((Q.n + kLbTq - 1) / kLbTq));
+    lb_matrix_kernel<<<grid, 256, kLbSmemBytes, st>>>(Q, R, qU, qL, rU, rL, cost, two_way, lb);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,19 +753,25 @@ int with_derivative(const eap_params* p, const eap_series_set* a, const eap_seri
 }
 
 // Shared body of 1-NN for device-resident sets.
+// keys_out (with key_offset) replaces out_idx / out_dist by packed keys.
 int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
-             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep) {
+             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep,
+             unsigned long long* keys_out = nullptr, long long key_offset = 0) {
     int rc = validate_params(p);
     if (rc) return rc;
     int mq = 0, mr = 0;
     if ((rc = validate_set(qs, &mq)) || (rc = validate_set(rs, &mr))) return rc;
-    if (qs->count > 0 && (!out_idx || !out_dist)) return EAP_EINVAL;
+    if (qs->count > 0 && !keys_out && (!out_idx || !out_dist)) return EAP_EINVAL;
     if (stats) std::memset(stats, 0, sizeof(*stats));
     const int nq = qs->count, nr = rs->count;
     if (nq == 0) return EAP_OK;
     const int sms = device_sms();
     if (sms <= 0) return EAP_EDEVICE;
     if (nr == 0) {
+        if (keys_out) {   // every key says "none": +inf bits, no index
+            keys_kernel<<<(nq + 255) / 256, 256, 0, st>>>(nullptr, nq, 0, keys_out, nullptr);
+            return cuda_status((int)cudaGetLastError());
+        }
         fill_nn_empty_kernel<<<(nq + 255) / 256, 256, 0, st>>>(out_idx, out_dist, nq);
         return cuda_status((int)cudaGetLastError());
     }
@@ -738,22 +863,25 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
         sort_seed_kernel<<<nq, 512, sizeof(unsigned long long) * chunk, st>>>(d_ub, nr, chunk, d_order, d_best);
         if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
     }
-    DpTimer tm(stats != nullptr);
+    DpTimer tm(stats != nullptr), tlb(stats != nullptr && use_lb);
     if (use_lb) {
+        tlb.start(st);
         KParams ke = make_kparams(p);
         ke.windowed = 1;
         if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }   // DTW: the whole series
         envelope_kernel<<<nq, 128, 0, st>>>(dev_set(qs, nullptr), ke, L.qU, L.qL);
         if (use_lb2) envelope_kernel<<<nr, 128, 0, st>>>(dev_set(rs, nullptr), ke, L.rU, L.rL);
-        lb_matrix_kernel<<<nq, 256, 0, st>>>(dev_set(qs, nullptr), dev_set(rs, nullptr), L.qU, L.qL, L.rU, L.rL, cost,
-                                             use_lb2 ? 1 : 0, L.lb);
+        launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), L.qU, L.qL, L.rU, L.rL, cost, use_lb2 ? 1 : 0,
+                         L.lb, st);
         if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
+        tlb.stop(st);
         c.job.lb = L.lb;
     }
     tm.start(st);
     if ((e = dispatch(c, false))) { sc.release(); return cuda_status(e); }
     tm.stop(st);
-    unpack_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq, out_idx, out_dist, d_stats);
+    if (keys_out) keys_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq, key_offset, keys_out, d_stats);
+    else unpack_kernel<<<(nq + 255) / 256, 256, 0, st>>>(d_best, nq, out_idx, out_dist, d_stats);
     if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
     unsigned long long h[kStatCount];
     if (stats || dev_stats_keep) {
@@ -769,6 +897,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
             stats->cells_computed = h[kStatCells];
             stats->cells_effective = sum_cells(qs, rs);
             stats->dp_ms = tm.ms();
+            stats->lb_ms = tlb.ms();
         }
         if (dev_stats_keep) std::memcpy(dev_stats_keep, h, sizeof(h));
         if (h[kStatErrors]) return EAP_EINTERNAL;
@@ -777,9 +906,10 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
 }
 
 int nn1_impl(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* out_idx,
-             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep) {
+             float* out_dist, cudaStream_t st, eap_stats* stats, unsigned long long* dev_stats_keep,
+             unsigned long long* keys_out = nullptr, long long key_offset = 0) {
     return with_derivative(p, qs, rs, st, [&](const eap_params* q, const eap_series_set* a, const eap_series_set* b) {
-        return nn1_core(q, a, b, out_idx, out_dist, st, stats, dev_stats_keep);
+        return nn1_core(q, a, b, out_idx, out_dist, st, stats, dev_stats_keep, keys_out, key_offset);
     });
 }
 
@@ -832,6 +962,27 @@ int32_t eap_version(void) { return 1; }
 int eap_nn1(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t* out_idx,
             float* out_dist, void* cuda_stream, eap_stats* opt_stats) {
     return nn1_impl(p, queries, refs, out_idx, out_dist, (cudaStream_t)cuda_stream, opt_stats, nullptr);
+}
+
+int eap_nn1_keys(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs,
+                 int64_t index_offset, uint64_t* out_keys, void* cuda_stream, eap_stats* opt_stats) {
+    if (!queries || !refs) return EAP_EINVAL;
+    if (queries->count > 0 && !out_keys) return EAP_EINVAL;
+    if (index_offset < 0 || index_offset + (int64_t)refs->count >= (int64_t)kNoIndex) return EAP_EINVAL;
+    return nn1_impl(p, queries, refs, nullptr, nullptr, (cudaStream_t)cuda_stream, opt_stats, nullptr,
+                    (unsigned long long*)out_keys, (long long)index_offset);
+}
+
+int eap_keys_unpack(const uint64_t* keys, int32_t n, int32_t* out_idx, float* out_dist, void* cuda_stream) {
+    if (n < 0) return EAP_EINVAL;
+    if (n == 0) return EAP_OK;
+    if (!keys || !out_idx || !out_dist) return EAP_EINVAL;
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    const int blocks = std::min((n + 255) / 256, sms * 8);
+    keys_unpack_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>((const unsigned long long*)keys, n, out_idx,
+                                                                        out_dist);
+    return cuda_status((int)cudaGetLastError());
 }
 
 int eap_nn1_host(const eap_params* p, const float* q_data, const int64_t* q_offsets, const int32_t* q_lengths,
@@ -1361,8 +1512,7 @@ void launch_lb(const eap_params* p, const eap_series_set* qs, const eap_series_s
     if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }
     envelope_kernel<<<qs->count, 128, 0, st>>>(dev_set(qs, nullptr), ke, qU, qL);
     if (two_way) envelope_kernel<<<rs->count, 128, 0, st>>>(dev_set(rs, nullptr), ke, rU, rL);
-    lb_matrix_kernel<<<qs->count, 256, 0, st>>>(dev_set(qs, nullptr), dev_set(rs, nullptr), qU, qL, rU, rL,
-                                                resolve_cost(p), two_way, lb);
+    launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), qU, qL, rU, rL, resolve_cost(p), two_way, lb, st);
 }
 KParams kparams_of(const eap_params* p) { return make_kparams(p); }
 int nn1_timed(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* idx, float* dist,

@@ -19,9 +19,12 @@
 // No warp ever spins on another.
 //
 // Pruning: the pair is abandoned as soon as every lane's frontier is dead
-// (Section 4: no live cell can be reached), and a warp whose panel frontier is
-// dead while its left neighbour has finished stops that panel early (pruning
-// on the right); its consumer then reads +inf past the last live row.
+// (Section 4: no live cell can be reached) -- the frontier being each lane's
+// newest cells, the live boundary rows its panel has not read yet, and the
+// live boundary rows waiting for each warp's next panel -- and a warp whose
+// panel frontier is dead while its left neighbour has finished stops that
+// panel early (pruning on the right); its consumer then reads +inf past the
+// last live row.
 #pragma once
 
 #include "eap_device.cuh"
@@ -216,11 +219,18 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                 }
             }
         }
-        if (!have && p < npan && lane == 0) {
-            // This warp's next panel has not started: live rows its producer has
-            // already written, or a live top border above it, are still frontier.
-            if (p > 0 && sh.live_hi[p - 1] > 0) dead = false;
-            if (hborder<F>(in, p * P) <= cut) dead = false;
+        if (lane == 0) {
+            // The next panel this warp has not started yet (the one after its
+            // current panel, or the one it waits for): live rows its producer
+            // has already written, or a live top border above it, are still
+            // frontier.  The producer can be far ahead of this warp: the last
+            // panel of a round starts 7 lags into the round, long before warp
+            // 0 finishes its panel of that round and takes up the next.
+            const int pn = have ? p + kCtaWarps : p;
+            if (pn < npan) {
+                if (pn > 0 && sh.live_hi[pn - 1] > 0) dead = false;
+                if (hborder<F>(in, pn * P) <= cut) dead = false;
+            }
         }
         if (threadIdx.x == 0) {
             if (PRUNE && in.cut_src) sh.cut_next = __uint_as_float((unsigned)(*(volatile const unsigned long long*)in.cut_src >> 32));

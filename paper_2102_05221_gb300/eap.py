@@ -46,10 +46,10 @@ class eap_series_set(ctypes.Structure):
 class eap_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("pairs_lb_pruned", ctypes.c_uint64),
                 ("pairs_abandoned", ctypes.c_uint64), ("cells_effective", ctypes.c_uint64),
-                ("cells_computed", ctypes.c_uint64), ("dp_ms", ctypes.c_double)]
+                ("cells_computed", ctypes.c_uint64), ("dp_ms", ctypes.c_double), ("lb_ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: (float(getattr(self, k)) if k == "dp_ms" else int(getattr(self, k))) for k, _ in self._fields_}
+        return {k: (float(getattr(self, k)) if k.endswith("_ms") else int(getattr(self, k))) for k, _ in self._fields_}
 
 
 class eap_serve_config(ctypes.Structure):
@@ -88,6 +88,9 @@ def load(build_if_missing: bool = True):
         lib.eap_pairs.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), vp, vp, vp, vp, i32, vp,
                                   P(eap_stats)]
         lib.eap_lb_keogh.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), vp, vp, vp, i32, vp]
+        lib.eap_nn1_keys.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), ctypes.c_int64, vp, vp,
+                                     P(eap_stats)]
+        lib.eap_keys_unpack.argtypes = [vp, i32, vp, vp, vp]
         if hasattr(lib, "eap_serve_create"):
             lib.eap_serve_create.argtypes = [P(eap_serve_config), P(ctypes.c_int)]
             lib.eap_serve_create.restype = vp
@@ -97,7 +100,8 @@ def load(build_if_missing: bool = True):
             lib.eap_serve_drain.argtypes = [vp, i32]
             lib.eap_serve_destroy.argtypes = [vp]
         lib.eap_subseq.argtypes = [P(eap_params), vp, ctypes.c_int64, P(eap_series_set), vp, vp, vp, P(eap_stats)]
-        for name in ("eap_nn1", "eap_nn1_host", "eap_pairwise", "eap_pairs", "eap_lb_keogh", "eap_subseq"):
+        for name in ("eap_nn1", "eap_nn1_host", "eap_pairwise", "eap_pairs", "eap_lb_keogh", "eap_subseq",
+                     "eap_nn1_keys", "eap_keys_unpack"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -197,6 +201,38 @@ def eap_nn1(p: eap_params, queries: SeriesSet, refs: SeriesSet, stream=None, wit
                      _stream_ptr(stream), ctypes.byref(st) if with_stats else None)
     _check(rc, "eap_nn1")
     return (idx, dist, st.as_dict()) if with_stats else (idx, dist)
+
+
+def eap_nn1_keys(p: eap_params, queries: SeriesSet, refs: SeriesSet, index_offset: int = 0, stream=None,
+                 with_stats: bool = False, out_keys=None):
+    """1-NN against one candidate shard as packed keys (int64 tensor on the
+    device): (D bits << 32) | (local index + index_offset); the element-wise
+    minimum over the shards is the 1-NN over their union."""
+    torch = _torch()
+    lib = load()
+    dev = queries.data.device
+    keys = out_keys if out_keys is not None else torch.empty(queries.count, dtype=torch.int64, device=dev)
+    qs, rs = queries.struct(), refs.struct()
+    st = eap_stats()
+    rc = lib.eap_nn1_keys(ctypes.byref(p), ctypes.byref(qs), ctypes.byref(rs), int(index_offset),
+                          ctypes.c_void_p(keys.data_ptr() if queries.count else 0), _stream_ptr(stream),
+                          ctypes.byref(st) if with_stats else None)
+    _check(rc, "eap_nn1_keys")
+    return (keys, st.as_dict()) if with_stats else keys
+
+
+def eap_keys_unpack(keys, stream=None, out_idx=None, out_dist=None):
+    """Keys of eap_nn1_keys to (idx int32, dist float32) device tensors."""
+    torch = _torch()
+    lib = load()
+    n = int(keys.numel())
+    idx = out_idx if out_idx is not None else torch.empty(n, dtype=torch.int32, device=keys.device)
+    dist = out_dist if out_dist is not None else torch.empty(n, dtype=torch.float32, device=keys.device)
+    rc = lib.eap_keys_unpack(ctypes.c_void_p(keys.data_ptr() if n else 0), n,
+                             ctypes.c_void_p(idx.data_ptr() if n else 0), ctypes.c_void_p(dist.data_ptr() if n else 0),
+                             _stream_ptr(stream))
+    _check(rc, "eap_keys_unpack")
+    return idx, dist
 
 
 def eap_nn1_host(p: eap_params, queries, refs, with_stats: bool = False, out_idx=None, out_dist=None):

@@ -11,6 +11,12 @@ smallest distance and, among equal distances, the lowest index (Alg. 1's
 strict "<" over candidates in index order).  Distances are >= 0 (or +inf),
 so their float bits order like the values and the key fits in a
 non-negative int64.
+
+On the GPU the keys never leave the device: ``eap_nn1_keys`` (the library's
+1-NN on this rank's slice, packed with global indices) -> one all-reduce MIN
+of an int64 tensor (NCCL on device memory; gloo through host memory) ->
+``eap_keys_unpack``.  The numpy helpers below are the same packing for host
+arrays.
 """
 from __future__ import annotations
 
@@ -66,3 +72,24 @@ def nn1_candidate_sharded(local_search, n_refs: int, rank: int, world: int, grou
     idx, dist = local_search(b, e)
     keys = allreduce_nn(pack_nn(idx, dist, b), group)
     return unpack_nn(keys)
+
+
+def nn1_candidate_sharded_gpu(p, queries, refs_local, index_offset: int, group=None, stream=None):
+    """1-NN over the union of every rank's candidate shard, on the product
+    path: this rank's shard (``refs_local``, global indices starting at
+    ``index_offset``) through eap_nn1_keys, the MIN all-reduce of the keys,
+    then eap_keys_unpack.  Returns (idx, dist) device tensors, identical on
+    every rank."""
+    import torch.distributed as dist
+
+    from . import eap
+    keys = eap.eap_nn1_keys(p, queries, refs_local, index_offset, stream=stream)
+    if dist.get_backend(group) == "nccl":
+        dist.all_reduce(keys, op=dist.ReduceOp.MIN, group=group)
+    else:
+        if stream is not None:
+            stream.synchronize()
+        host = keys.cpu()
+        dist.all_reduce(host, op=dist.ReduceOp.MIN, group=group)
+        keys.copy_(host)
+    return eap.eap_keys_unpack(keys, stream=stream)

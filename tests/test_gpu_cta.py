@@ -72,3 +72,57 @@ def test_cta_nn1_and_pairwise(kind):
     mw = _with_map("warp", lambda: eap.eap_pairwise(p, S, eap.EAP_PRUNE_ONLY).cpu().numpy())
     mc = _with_map("cta", lambda: eap.eap_pairwise(p, S, eap.EAP_PRUNE_ONLY).cpu().numpy())
     assert np.array_equal(mw, mc)
+
+
+@pytest.mark.parametrize("kind", UNWINDOWED)
+def test_cta_nn1_at_8192_against_full_oracle_rows(kind):
+    """L = 8192, the length the CTA mapping exists for (the default from 6144
+    up): 1-NN of 2 queries among 48 candidates against the oracle's complete
+    distance rows (every candidate, FP64), and bit-identical to the warp
+    mapping.  (This test found the CTA abandoning vote ignoring live boundary
+    rows that wait for a busy warp's next panel.)"""
+    from paper_2102_05221_gb300 import eap
+    ds = synth.make_dataset(48, 2, 8192, 3, 8192 + UNWINDOWED.index(kind))
+    tr, te = synth.pack(ds.train), synth.pack(ds.test)
+    R, Q = eap.SeriesSet.from_packed(tr), eap.SeriesSet.from_packed(te)
+    kw = WORKLOAD_PARAMS[kind]
+    if kind == "wdtw":
+        # g = 0.05 at L = 8192 puts every weight near exp(-205): below the
+        # float32 range, all distances round to 0.  g = 0.01 keeps them in range.
+        kw = dict(kw, wdtw_g=0.01)
+    p = gpu_params(eap, kind, **kw)
+    ic, dc = eap.eap_nn1(p, Q, R)                       # default mapping: CTA at this length
+    ic2, dc2 = _with_map("cta", lambda: eap.eap_nn1(p, Q, R))
+    iw, dw = _with_map("warp", lambda: eap.eap_nn1(p, Q, R))
+    for i, d in ((ic2, dc2), (iw, dw)):
+        assert np.array_equal(i.cpu().numpy(), ic.cpu().numpy())
+        assert np.array_equal(d.cpu().numpy(), dc.cpu().numpy())
+    D = O.cross(oracle_params(kind, **kw), te, tr)
+    check_nn(ic.cpu().numpy(), dc.cpu().numpy(), D)
+
+
+@pytest.mark.parametrize("W", ["4", "8"])
+@pytest.mark.parametrize("L", [7168, 8192])
+def test_cta_explicit_cutoffs_at_long_lengths(W, L):
+    """Explicit cut-offs from D to 10 D on every pair of 2 x 48 series at
+    7168 and 8192 points (several rounds of eight panels): the CTA mapping
+    returns D exactly when D <= cut-off, for both strip widths."""
+    from paper_2102_05221_gb300 import eap
+    ds = synth.make_dataset(48, 2, 8192, 3, 8192)
+    A = eap.SeriesSet.from_matrix(ds.test[:, :L])
+    B = eap.SeriesSet.from_matrix(ds.train[:, :L])
+    ia = np.repeat(np.arange(2), 48).astype(np.int32)
+    ib = np.tile(np.arange(48), 2).astype(np.int32)
+    old = os.environ.get("EAP_W")
+    os.environ["EAP_W"] = W
+    try:
+        base = _with_map("cta", lambda: eap.eap_pairs(eap.params("dtw", prune=0), A, B, ia, ib).cpu().numpy())
+        for sc in (1.0, 1.2, 1.5, 2.0, 3.0, 5.0, 10.0):
+            cut = (base * np.float32(sc)).astype(np.float32)
+            got = _with_map("cta", lambda: eap.eap_pairs(eap.params("dtw", prune=1), A, B, ia, ib, cut).cpu().numpy())
+            assert np.array_equal(got, base), (W, L, sc, np.flatnonzero(got != base)[:6])
+    finally:
+        if old is None:
+            os.environ.pop("EAP_W", None)
+        else:
+            os.environ["EAP_W"] = old
