@@ -842,7 +842,7 @@ def workload_uneven_64(args):
             eap.eap_nn1(p, Q1, R)
     t_single = _sync_time(run_singles, reps=1)
     q_single = len(singles) / (t_single / 1e3)
-    return {"metric": "batched uneven 1-NN queries/s (64 datasets, CDTW+LB_Keogh2, ERP, TWE), one graph-captured launch",
+    return {"metric": "batched uneven 1-NN queries/s (64 datasets, CDTW+LB_Keogh2, ERP, TWE), one graph-captured eap_nn1_batch call",
             "value": q_batch, "unit": "queries/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "ms_per_step": t_batch, "steps": args.steps,
             "config": {"workload": "uneven_64_datasets_L24_2048", "tasks": len(tasks), "queries_per_step": nq},
@@ -864,7 +864,7 @@ def workload_serving(args):
     refsets = synth.serving_refsets(sizes)
     qpool = {L: synth.random_walks(np.random.default_rng(77 + i), 64, L if L != "mixed" else 512).astype(np.float32)
              for i, L in enumerate(sizes)}
-    rates = [50, 100, 200, 1000, 5000, 20000, 50000]
+    rates = [50, 100, 200, 400, 1000, 5000, 20000, 50000]
     duration = 1.5
     kinds = list(KIND_PARAMS)
     params = {k: eap.params(k, **KIND_PARAMS[k]) for k in kinds}
@@ -902,11 +902,46 @@ def workload_serving(args):
             out[str(rate)] = {"offered_per_s": n / arrivals[-1], "admitted": st["submitted"], "rejected": st["rejected"],
                               "completed_per_s": st["completed"] / t_end, "p50_ms": st["lat_p50_ms"],
                               "p99_ms": st["lat_p99_ms"], "batches": st["batches"]}
+        # Per-set capacity, closed loop: M queries of one set (distances in
+        # turn) submitted as fast as admission allows, against the same
+        # queries as one eap_nn1 launch each (synchronised, plain EAPruned).
+        per_set = {}
+        import torch
+        gsets = {L: eap.SeriesSet.from_packed(p) for L, p in refsets.items()}
+        m_of = {128: 192, 256: 192, 512: 96, 1024: 48, 2048: 24, 4096: 12, 8192: 6, "mixed": 192}
+        for L in keys:
+            m = m_of.get(L, 24)
+            qs = [(kinds[i % len(kinds)], qpool[L][i % 64]) for i in range(m)]
+            srv.stats(reset=True)
+            t0 = time.perf_counter()
+            tickets = []
+            for kind, q in qs:
+                while True:
+                    t = srv.submit(sids[L], params[kind], q)
+                    if t is not None:
+                        break
+                    time.sleep(0.0002)
+                tickets.append(t)
+            srv.drain(600000)
+            served = m / (time.perf_counter() - t0)
+            for t in tickets:
+                srv.poll(t)
+            st = srv.stats(reset=True)
+            singles = [(params[kind], eap.SeriesSet.from_matrix(q[None, :])) for kind, q in qs]
+            for p1, Q1 in singles[:6]:
+                eap.eap_nn1(p1, Q1, gsets[L])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for p1, Q1 in singles:
+                eap.eap_nn1(p1, Q1, gsets[L])
+                torch.cuda.synchronize()
+            single = m / (time.perf_counter() - t0)
+            per_set[str(L)] = {"queries": m, "served_per_s": served, "one_launch_per_query_per_s": single,
+                               "speedup": served / single, "batches": st["batches"],
+                               "p50_ms": st["lat_p50_ms"], "p99_ms": st["lat_p99_ms"]}
     best = max(v["completed_per_s"] for v in out.values())
     # One launch per query (plain eap_nn1 on one query at a time) on the same
     # mix of sets and distances, as the baseline for batching.
-    import torch
-    gsets = {L: eap.SeriesSet.from_packed(p) for L, p in refsets.items()}
     rng2 = np.random.default_rng(9)
     sample = [(keys[int(rng2.integers(0, len(keys)))], kinds[int(rng2.integers(0, len(kinds)))],
                int(rng2.integers(0, 64))) for _ in range(96)]
@@ -924,7 +959,7 @@ def workload_serving(args):
             "config": {"workload": "serving_8_sets", "sizes": {str(k): v for k, v in sizes.items()},
                        "duration_s_per_rate": duration, "max_inflight": 128}, "per_rate": out,
             "one_launch_per_query": {"value": single_qps, "unit": "queries/s", "sample_queries": len(singles)},
-            "speedup_vs_one_launch_per_query": best / single_qps}
+            "speedup_vs_one_launch_per_query": best / single_qps, "per_set_closed_loop": per_set}
 
 
 def run_other_workload(args):

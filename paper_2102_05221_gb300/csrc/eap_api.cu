@@ -1515,6 +1515,50 @@ void launch_lb(const eap_params* p, const eap_series_set* qs, const eap_series_s
     launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), qU, qL, rU, rL, resolve_cost(p), two_way, lb, st);
 }
 KParams kparams_of(const eap_params* p) { return make_kparams(p); }
+// The EAPruned 1-NN DP of one task on its own pre-computed order, seeds and
+// bounds (the batched path's per-task launch): the same mapping choice as
+// eap_nn1 -- CTA per pair for long unwindowed series (autotuned or default),
+// band coordinates for the windowed distances, 16-lane groups, or a warp per
+// pair -- so a batch runs every task on the kernel eap_nn1 would use.
+int nn1_dp_launch(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, const float* bq,
+                  const float* br, const float* wt, const int32_t* order, unsigned long long* best, const float* lb,
+                  float4* rowpack, unsigned long long* counter, unsigned long long* stats, int max_rows, int max_cols,
+                  cudaStream_t st) {
+    const int sms = device_sms();
+    if (sms <= 0) return EAP_EDEVICE;
+    const int cost = resolve_cost(p);
+    eaph::LaunchCtx c;
+    std::memset(&c, 0, sizeof(c));
+    c.job.mode = kModeNN1;
+    c.job.A = dev_set(qs, bq);
+    c.job.B = dev_set(rs, br);
+    c.job.nitems = (unsigned long long)qs->count * rs->count;
+    c.job.counter = counter;
+    c.job.order = order;
+    c.job.best = best;
+    c.job.stats = stats;
+    c.job.wdtw_table = wt;
+    c.job.lb = lb;
+    c.job.bnd_stride = ((max_rows + 1) + 31) & ~31;
+    c.kp = make_kparams(p);
+    c.kp.wdtw_w = wt;
+    c.rowpack = rowpack;
+    c.kind = p->kind;
+    c.cost = cost;
+    c.prune = kPmPruned;
+    c.sms = sms;
+    c.max_rows = max_rows;
+    c.max_cols = max_cols;
+    c.cta = choose_cta(p->kind, cost, max_rows, max_cols, c.prune);
+    choose_w_group(p->kind, cost, max_rows, max_cols, c.prune, &c.W, &c.group);
+    if (c.cta) { c.W = choose_w(p->kind, cost, max_cols, c.prune); c.group = 0; }
+    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(max_rows, max_cols),
+                &c.band, &c.band_g, &c.band_exact);
+    c.stream = st;
+    return cuda_status(dispatch(c, false));
+}
+
+
 int nn1_timed(const eap_params* p, const eap_series_set* qs, const eap_series_set* rs, int32_t* idx, float* dist,
               cudaStream_t st, double* dp_ms) {
     eap_stats s;

@@ -1,15 +1,17 @@
-// eap_batch.cu -- many 1-NN problems in one persistent DP launch
-// (eap_nn1_batch) and the strip-width autotuner (eap_autotune).
+// eap_batch.cu -- many 1-NN problems in one call (eap_nn1_batch) and the
+// mapping autotuner (eap_autotune).
 //
-// Every task (queries, references, one distance and its parameters) becomes
-// a contiguous range of (rank, query) work items; tasks are placed longest
-// series first, so the long pairs start early and the short ones fill the
-// tail of the launch.  One warp-per-pair kernel serves every task: each item
-// picks its distance's functor and strip width at run time (uniform across
-// the warp), so DTW, CDTW, WDTW, ERP, MSM and TWE datasets of any length mix
-// in the same work queue.  The pre-passes (diagonal upper bounds, candidate
-// sort and cut-off seed, result unpack) are one launch each over all tasks;
-// only ERP borders, WDTW tables and LB_Keogh envelopes run per task.
+// Every task (queries, references, one distance and its parameters) is a
+// 1-NN search of its own.  The pre-passes run as one launch each over all
+// tasks: cut-off init, the diagonal upper bound of every (query, candidate)
+// pair, the per-query candidate sort with the cut-off seed, and the result
+// unpack.  The DP then runs task by task, longest series first, each as one
+// persistent launch of the kernel eap_nn1 would pick for it -- CTA per pair
+// for long unwindowed series (by the autotuned table or the default), band
+// coordinates for the windowed distances, 16-lane groups or a warp per pair
+// otherwise -- with the strip width of the autotuned table.  Everything is
+// enqueued on the caller's stream with stream-ordered scratch and no host
+// synchronisation, so the whole call can be captured in one CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,7 +56,7 @@ struct TaskDev {
     float* out_dist;
     unsigned long long begin;    // first work item of the task
     int qbegin;                  // first query of the task in the batch numbering
-    int fn, W, nq, nr;
+    int fn, nq, nr;
 };
 
 constexpr int kUploadChunk = 96;   // tasks per parameter block (kernel parameters are limited to ~32 KB)
@@ -99,24 +101,6 @@ __device__ void fill_pair(const TaskDev& T, int q, int c, PairIn& in) {
     in.rp = T.rp ? T.rp + oa : nullptr;
     in.w = pair_window(T.kp, in.La, in.Lb);
     in.cut = EAP_FINF;
-}
-
-template <int W>
-__device__ float pair_by_fn(int fn, const PairIn& in, float* bnd, const KParams& kp, unsigned long long& cells,
-                            bool& ab) {
-    switch (fn) {
-        case kFnDtwSq: return warp_pair<FDtw<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        case kFnDtwAbs: return warp_pair<FDtw<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        case kFnCdtwSq: return warp_pair<FDtw<0>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
-        case kFnCdtwAbs: return warp_pair<FDtw<1>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
-        case kFnWdtwSq: return warp_pair<FWdtw<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        case kFnWdtwAbs: return warp_pair<FWdtw<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        case kFnErpSq: return warp_pair<FErp<0>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
-        case kFnErpAbs: return warp_pair<FErp<1>, W, kPmPruned, true>(in, bnd, kp, cells, ab);
-        case kFnMsm: return warp_pair<FMsm, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        case kFnTweSq: return warp_pair<FTwe<0>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-        default: return warp_pair<FTwe<1>, W, kPmPruned, false>(in, bnd, kp, cells, ab);
-    }
 }
 
 template <class F>
@@ -193,53 +177,6 @@ __global__ void batch_sort_kernel(const TaskDev* __restrict__ T, int nt) {
     if (threadIdx.x == 0) t.best[q] = nb > 0 ? (((gmin >> 32) << 32) | kNoIndex) : pack_best(EAP_FINF, kNoIndex);
 }
 
-__global__ void __launch_bounds__(kThreads) batch_dp_kernel(const TaskDev* __restrict__ T, int nt,
-                                                            unsigned long long nitems, unsigned long long* counter,
-                                                            int bnd_stride, unsigned long long* stats) {
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    float* bnd = smem + (threadIdx.x >> 5) * bnd_stride;
-    unsigned long long cells = 0, npairs = 0, nab = 0, nlb = 0;
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(counter, 1ULL);
-        item = __shfl_sync(EAP_FULL, item, 0);
-        if (item >= nitems) break;
-        const TaskDev& t = T[find_task_item(T, nt, item)];
-        const unsigned long long local = item - t.begin;
-        const unsigned long long rank = local / (unsigned)t.nq;
-        const int q = (int)(local - rank * (unsigned)t.nq);
-        const int c = t.order[(size_t)q * t.nr + rank];
-        unsigned long long cv = 0;
-        if (lane == 0) cv = *(volatile const unsigned long long*)(t.best + q);
-        cv = __shfl_sync(EAP_FULL, cv, 0);
-        const float cut = __uint_as_float((unsigned)(cv >> 32));
-        if (t.lb && t.lb[(size_t)q * t.nr + c] > cut) { ++nlb; continue; }
-        PairIn in;
-        fill_pair(t, q, c, in);
-        in.cut = cut;
-        bool ab = false;
-        float d;
-        if (in.w < abs(in.La - in.Lb)) { d = EAP_FINF; ab = true; }
-        else if (t.W == 4) d = pair_by_fn<4>(t.fn, in, bnd, t.kp, cells, ab);
-        else d = pair_by_fn<8>(t.fn, in, bnd, t.kp, cells, ab);
-        ++npairs;
-        nab += ab ? 1 : 0;
-        if (lane == 0 && d != EAP_FINF) atomicMin(t.best + q, pack_best(d, (unsigned)c));
-        __syncwarp();
-    }
-    if (stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cells += __shfl_xor_sync(EAP_FULL, cells, o);
-        if (lane == 0) {
-            if (npairs) atomicAdd(stats + kStatPairs, npairs);
-            if (nab) atomicAdd(stats + kStatAbandoned, nab);
-            if (cells) atomicAdd(stats + kStatCells, cells);
-            if (nlb) atomicAdd(stats + kStatLbPruned, nlb);
-        }
-    }
-}
-
 __global__ void batch_unpack_kernel(const TaskDev* __restrict__ T, int nt, int total_q, unsigned long long* stats) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_q; g += gridDim.x * blockDim.x) {
         const TaskDev& t = T[find_task_query(T, nt, g)];
@@ -260,7 +197,7 @@ __global__ void batch_unpack_kernel(const TaskDev* __restrict__ T, int nt, int t
 
 struct HostTask {
     int src;            // index in the caller's array
-    int fn, W, cost;
+    int fn, cost;
     int nq, nr, mq, mr;
     bool erp, wdtw, lb, lb2, deriv, packed;
 };
@@ -279,7 +216,6 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
     if (opt_stats) std::memset(opt_stats, 0, sizeof(*opt_stats));
     cudaStream_t st = (cudaStream_t)cuda_stream;
     std::vector<HostTask> ht;
-    int max_rows = 0;
     for (int i = 0; i < ntasks; ++i) {
         const eap_nn1_task& tk = tasks[i];
         int rc = eaph::validate_params_ext(&tk.params);
@@ -293,7 +229,6 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         h.src = i;
         h.cost = eaph::resolve_cost_ext(&tk.params);
         h.fn = fn_of(tk.params.kind, h.cost);
-        h.W = eaph::pick_w(tk.params.kind, h.cost, mr, 1) >= 8 ? 8 : 4;   // the batch kernel is built for W = 4, 8
         h.nq = tk.queries.count;
         h.nr = tk.refs.count;
         h.mq = mq;
@@ -305,7 +240,6 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         h.deriv = tk.params.derivative != 0;
         h.packed = eaph::kind_packed(tk.params.kind);
         ht.push_back(h);
-        max_rows = std::max(max_rows, mq);
     }
     const int sms = device_sms_b();
     if (sms <= 0) return EAP_EDEVICE;
@@ -322,7 +256,7 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
     size_t used = 0;
     auto take = [&](size_t bytes) { const size_t o = (used + 255) & ~(size_t)255; used = o + bytes; return o; };
     const size_t o_tasks = take(sizeof(TaskDev) * nt);
-    const size_t o_ctr = take(sizeof(unsigned long long));
+    const size_t o_ctr = take(sizeof(unsigned long long) * nt);   // one work-queue head per task
     const size_t o_stats = take(sizeof(unsigned long long) * kStatCount);
     struct Off { size_t best, ub, order, lb, qU, qL, rU, rL, bq, br, wt, dq, dr, rp; };
     std::vector<Off> off(nt);
@@ -397,7 +331,6 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         t.begin = items;
         t.qbegin = total_q;
         t.fn = h.fn;
-        t.W = h.W;
         t.nq = h.nq;
         t.nr = h.nr;
         items += (unsigned long long)h.nq * h.nr;
@@ -415,9 +348,15 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         for (int i = 0; i < ch.n; ++i) ch.t[i] = td[b0 + i];
         upload_tasks_kernel<<<1, 128, 0, st>>>(ch, d_tasks);
     }
-    e |= (int)cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long), st);
+    e |= (int)cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * nt, st);
     e |= (int)cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * kStatCount, st);
     batch_init_kernel<<<(total_q + 255) / 256, 256, 0, st>>>(d_tasks, nt, total_q);
+    // DP time (stats only: events are not created for calls without stats).
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (opt_stats && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)) {
+        cudaGetLastError();
+        ev[0] = ev[1] = nullptr;
+    }
     for (int k = 0; k < nt; ++k) {
         const HostTask& h = ht[k];
         const eap_nn1_task& tk = tasks[h.src];
@@ -427,9 +366,6 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
             eaph::launch_erp_border(&rset[k], tk.params.erp_gap, h.cost, (float*)(base + o.br), st);
         }
         if (h.wdtw) eaph::launch_wdtw_table((float*)(base + o.wt), tk.params.wdtw_g, tk.params.wdtw_wmax, st);
-        if (h.packed)
-            e |= eaph::launch_rowpack(tk.params.kind, h.cost, &qset[k], eaph::kparams_of(&tk.params),
-                                      (float4*)(base + o.rp), st);
         if (h.lb && h.nr > 0)
             eaph::launch_lb(&tk.params, &qset[k], &rset[k], h.lb2 ? 1 : 0, (float*)(base + o.qU), (float*)(base + o.qL),
                             h.lb2 ? (float*)(base + o.rU) : nullptr, h.lb2 ? (float*)(base + o.rL) : nullptr,
@@ -443,22 +379,34 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
         int chunk = 1;
         while (chunk < max_nr && chunk < 4096) chunk <<= 1;
         batch_sort_kernel<<<total_q, 512, sizeof(unsigned long long) * chunk, st>>>(d_tasks, nt);
-        const int stride = ((max_rows + 1) + 31) & ~31;
-        const size_t smem = (size_t)kWarpsPerBlock * stride * sizeof(float);
-        if (smem > 48 * 1024) e |= (int)cudaFuncSetAttribute(batch_dp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        e |= (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_dp_kernel, kThreads, smem);
-        unsigned long long grid = (unsigned long long)std::max(per_sm, 1) * sms;
-        grid = std::min(grid, (items + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        batch_dp_kernel<<<(unsigned)std::max<unsigned long long>(grid, 1), kThreads, smem, st>>>(d_tasks, nt, items, d_ctr,
-                                                                                                   stride, d_stats);
+        // The DP, task by task (longest series first), each on eap_nn1's kernel
+        // for it; the packed row constants are computed by that launch.
+        if (ev[0]) cudaEventRecord(ev[0], st);
+        for (int k = 0; k < nt && !e; ++k) {
+            const HostTask& h = ht[k];
+            if (h.nr == 0) continue;
+            const eap_nn1_task& tk = tasks[h.src];
+            const Off& o = off[k];
+            const int rc = eaph::nn1_dp_launch(&tk.params, &qset[k], &rset[k],
+                                               h.erp ? (const float*)(base + o.bq) : nullptr,
+                                               h.erp ? (const float*)(base + o.br) : nullptr,
+                                               h.wdtw ? (const float*)(base + o.wt) : nullptr, td[k].order, td[k].best,
+                                               td[k].lb, h.packed ? (float4*)(base + o.rp) : nullptr, d_ctr + k, d_stats,
+                                               h.mq, h.mr, st);
+            if (rc) e |= 1;
+        }
+        if (ev[1]) cudaEventRecord(ev[1], st);
     }
     batch_unpack_kernel<<<(total_q + 255) / 256, 256, 0, st>>>(d_tasks, nt, total_q, d_stats);
     e |= (int)cudaGetLastError();
     unsigned long long hs[kStatCount];
     if (!e && opt_stats) e |= (int)cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(base, st);
-    if (e) return EAP_EDEVICE;
+    if (e) {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        return EAP_EDEVICE;
+    }
     if (opt_stats) {
         if (cudaStreamSynchronize(st) != cudaSuccess) return EAP_EDEVICE;
         opt_stats->pairs = hs[kStatPairs] + hs[kStatLbPruned];
@@ -474,6 +422,10 @@ extern "C" int eap_nn1_batch(const eap_nn1_task* tasks, int32_t ntasks, void* cu
             eff += a * b;
         }
         opt_stats->cells_effective = eff;
+        float ms = 0.f;
+        if (ev[0] && ev[1] && cudaEventElapsedTime(&ms, ev[0], ev[1]) == cudaSuccess) opt_stats->dp_ms = ms;
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
         if (hs[kStatErrors]) return EAP_EINTERNAL;
     }
     return EAP_OK;

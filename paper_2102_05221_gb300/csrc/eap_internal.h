@@ -73,6 +73,11 @@ int launch_rowpack(int kind, int cost, const ::eap_series_set* s, const eapd::KP
 void launch_lb(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int two_way,
                float* qU, float* qL, float* rU, float* rL, float* lb, cudaStream_t st);
 eapd::KParams kparams_of(const ::eap_params* p);
+// One task's EAPruned 1-NN DP launch with eap_nn1's mapping choice (eap_api.cu).
+int nn1_dp_launch(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, const float* bq,
+                  const float* br, const float* wt, const int32_t* order, unsigned long long* best, const float* lb,
+                  float4* rowpack, unsigned long long* counter, unsigned long long* stats, int max_rows, int max_cols,
+                  cudaStream_t st);
 int nn1_timed(const ::eap_params* p, const ::eap_series_set* qs, const ::eap_series_set* rs, int32_t* idx,
               float* dist, cudaStream_t st, double* dp_ms);
 

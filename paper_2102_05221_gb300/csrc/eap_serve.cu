@@ -4,14 +4,21 @@
 // single 1-NN queries (any length, any distance) from host memory; a query is
 // admitted only while the number of queries in flight and their HBM footprint
 // (query bytes + per-candidate scratch of the 1-NN search) stay inside the
-// configured budget, otherwise the submit answers EAP_EAGAIN.  A worker
-// thread forms batches continuously, least work first: every admitted query
-// with the same reference set and the same parameters joins one batch, each
-// batch runs as one eap_nn1 search (the persistent work-queue DP) on one of
-// several streams, and new batches are launched while earlier ones are still on the
-// GPU, so their work overlaps.  A result is the same float32 distance and
-// index whether its query runs alone or in a batch: the DP's value of a pair
-// does not depend on the cut-off it ran with, and ties go to the lowest index.
+// configured budget, otherwise the submit answers EAP_EAGAIN.
+//
+// Continuous batching: a worker thread keeps up to kSlots launches in flight,
+// each on its own stream.  Whenever a slot is free it takes the pending query
+// with the least work (query length x set elements) -- or the oldest one, once
+// it has waited kMaxWaitMs -- and with it every pending query of the same work
+// class (at most kClassFactor times the lead's work), whatever its reference
+// set or distance.  Those queries are grouped by (set, parameters) into tasks
+// and run as one eap_nn1_batch call: one pass of upper bounds, candidate sort
+// and cut-off seeds over all of them, then each task's DP on the kernel
+// eap_nn1 would pick.  Queries that arrive while launches are on the GPU join
+// the next free slot, so their work overlaps the running ones.  A result is
+// the same float32 distance and index whether its query runs alone or in a
+// batch: the DP's value of a pair does not depend on the cut-off it ran with,
+// and ties go to the lowest index.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,9 +39,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr int kSlots = 8;                    // streams with a batch in flight
+constexpr int kSlots = 8;                    // streams with a launch in flight
 constexpr int kBatchMaxQueries = 512;
-constexpr int64_t kBatchMaxFloats = 1 << 22; // query floats per batch (16 MiB)
+constexpr int64_t kBatchMaxFloats = 1 << 22; // query floats per launch (16 MiB)
+constexpr double kClassFactor = 4.0;         // a launch takes queries with up to this much the lead's work
+constexpr double kMaxWaitMs = 200.0;         // a query waiting this long leads the next launch
 
 struct RefSet {
     float* d_data = nullptr;
@@ -117,27 +126,26 @@ int64_t query_footprint(const eap_server* s, int32_t set_id, int32_t len) {
 }  // namespace
 
 bool eap_server::launch(Slot& sl) {
-    // Take the oldest pending query and every other pending query with the
-    // same reference set and parameters, up to the batch limits.
     std::vector<Req> batch;
-    RefSet rs_view;   // pointers and host mirrors of the batch's resident set (copied under the lock)
+    std::vector<RefSet> views;   // pointers and host mirrors of the resident sets the launch reads
+    std::vector<int32_t> view_of_set;
     {
         std::lock_guard<std::mutex> lk(mu);
         if (pending.empty()) return false;
-        // Least work first: the pending query with the fewest cells against its
-        // set (query length x set elements) leads the next batch, so short
-        // queries are not queued behind long ones; ties keep arrival order.
         auto work = [&](const Req& r) { return (double)r.q.size() * (double)sets[r.set_id].data_len; };
+        // Lead: the oldest query once it has waited kMaxWaitMs, else the least work.
+        const auto now = Clock::now();
         auto lead = pending.begin();
-        for (auto it = pending.begin(); it != pending.end(); ++it)
-            if (work(*it) < work(*lead)) lead = it;
-        const Req& head = *lead;
-        const int32_t set_id = head.set_id;
-        const eap_params p = head.p;
-        int64_t floats = 0;
+        if (std::chrono::duration<double, std::milli>(now - lead->t0).count() < kMaxWaitMs) {
+            for (auto it = pending.begin(); it != pending.end(); ++it)
+                if (work(*it) < work(*lead)) lead = it;
+        }
+        const double lead_work = work(*lead);
+        int64_t floats = (int64_t)lead->q.size();
+        batch.push_back(std::move(*lead));
+        pending.erase(lead);
         for (auto it = pending.begin(); it != pending.end() && (int)batch.size() < kBatchMaxQueries;) {
-            if (it->set_id == set_id && same_params(it->p, p) &&
-                (batch.empty() || floats + (int64_t)it->q.size() <= kBatchMaxFloats)) {
+            if (work(*it) <= lead_work * kClassFactor && floats + (int64_t)it->q.size() <= kBatchMaxFloats) {
                 floats += (int64_t)it->q.size();
                 batch.push_back(std::move(*it));
                 it = pending.erase(it);
@@ -145,18 +153,27 @@ bool eap_server::launch(Slot& sl) {
                 ++it;
             }
         }
-        if (!batch.empty()) {
-            const RefSet& r = sets[set_id];
-            rs_view.d_data = r.d_data;
-            rs_view.d_off = r.d_off;
-            rs_view.d_len = r.d_len;
-            rs_view.h_off = r.h_off;
-            rs_view.h_len = r.h_len;
-            rs_view.data_len = r.data_len;
-            rs_view.count = r.count;
+        view_of_set.assign(sets.size(), -1);
+        for (const Req& r : batch) {
+            if (view_of_set[r.set_id] >= 0) continue;
+            view_of_set[r.set_id] = (int32_t)views.size();
+            const RefSet& rs = sets[r.set_id];
+            RefSet v;
+            v.d_data = rs.d_data;
+            v.d_off = rs.d_off;
+            v.d_len = rs.d_len;
+            v.h_off = rs.h_off;
+            v.h_len = rs.h_len;
+            v.data_len = rs.data_len;
+            v.count = rs.count;
+            views.push_back(std::move(v));
         }
     }
-    if (batch.empty()) return false;
+    // Group the queries by (set, parameters): each group is one task.
+    std::stable_sort(batch.begin(), batch.end(), [](const Req& x, const Req& y) {
+        if (x.set_id != y.set_id) return x.set_id < y.set_id;
+        return std::memcmp(&x.p, &y.p, sizeof(eap_params)) < 0;
+    });
     const int nq = (int)batch.size();
     int64_t off = 0;
     for (int i = 0; i < nq; ++i) {
@@ -169,10 +186,23 @@ bool eap_server::launch(Slot& sl) {
     e |= (int)cudaMemcpyAsync(sl.d_q, sl.h_q, sizeof(float) * off, cudaMemcpyHostToDevice, sl.st);
     e |= (int)cudaMemcpyAsync(sl.d_off, sl.h_off, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, sl.st);
     e |= (int)cudaMemcpyAsync(sl.d_len, sl.h_len, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, sl.st);
-    const RefSet& rs = rs_view;
-    eap_series_set qs{sl.d_q, sl.d_off, sl.d_len, sl.h_off, sl.h_len, off, nq, 0};
-    eap_series_set rset{rs.d_data, rs.d_off, rs.d_len, rs.h_off.data(), rs.h_len.data(), rs.data_len, rs.count, 0};
-    int rc = e ? EAP_EDEVICE : eaph::nn1_device(&batch[0].p, &qs, &rset, sl.d_idx, sl.d_dist, sl.st);
+    int rc = e ? EAP_EDEVICE : EAP_OK;
+    std::vector<eap_nn1_task> tasks;
+    for (int b0 = 0; b0 < nq && rc == EAP_OK;) {
+        int b1 = b0 + 1;
+        while (b1 < nq && batch[b1].set_id == batch[b0].set_id && same_params(batch[b1].p, batch[b0].p)) ++b1;
+        const RefSet& rs = views[view_of_set[batch[b0].set_id]];
+        eap_series_set qs{sl.d_q, sl.d_off + b0, sl.d_len + b0, sl.h_off + b0, sl.h_len + b0, off, b1 - b0, 0};
+        eap_series_set rset{rs.d_data, rs.d_off, rs.d_len, rs.h_off.data(), rs.h_len.data(), rs.data_len, rs.count, 0};
+        if (batch[b0].p.prune == 1) {
+            tasks.push_back(eap_nn1_task{batch[b0].p, qs, rset, sl.d_idx + b0, sl.d_dist + b0});
+        } else {
+            // Base, EABase and Prune groups run as their own search.
+            rc = eaph::nn1_device(&batch[b0].p, &qs, &rset, sl.d_idx + b0, sl.d_dist + b0, sl.st);
+        }
+        b0 = b1;
+    }
+    if (rc == EAP_OK && !tasks.empty()) rc = eap_nn1_batch(tasks.data(), (int32_t)tasks.size(), sl.st, nullptr);
     if (rc == EAP_OK) {
         e = (int)cudaMemcpyAsync(sl.h_idx, sl.d_idx, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, sl.st);
         e |= (int)cudaMemcpyAsync(sl.h_dist, sl.d_dist, sizeof(float) * nq, cudaMemcpyDeviceToHost, sl.st);

@@ -1,6 +1,7 @@
 """Batched uneven workload: many datasets of different lengths and distances
-in one persistent launch (eap_nn1_batch), the autotuner, and CUDA-graph
-capture of the whole batch."""
+in one call (eap_nn1_batch: batched pre-passes, then each task's DP on the
+kernel eap_nn1 picks for it), the autotuner, and CUDA-graph capture of the
+whole batch."""
 import numpy as np
 import pytest
 
@@ -91,3 +92,44 @@ def test_autotune_picks_a_width_and_keeps_results(tmp_path):
         D = O.cross(oracle_params(kind, **kw), te, tr)
         check_nn(i1.cpu().numpy(), d1.cpu().numpy(), D)
     eap.eap_autotune_reset()
+
+
+def test_batch_runs_each_task_on_eap_nn1s_mapping():
+    """A batch mixing the mappings: CDTW at 512 points (exact band launch),
+    MSM (16-lane groups), DTW at 6200 points (CTA per pair by default), and a
+    2500-point TWE task with the CTA mapping forced by the map override.  The
+    batch must give the per-task eap_nn1 results bit for bit (same kernels,
+    same candidate order and seeds) and agree with the oracle."""
+    import os
+
+    import torch
+
+    from paper_2102_05221_gb300 import eap
+    specs = [("cdtw", {"window_ratio": 0.1}, 512, 60, 6), ("msm", {"msm_c": 0.5}, 300, 50, 5),
+             ("dtw", {}, 6200, 12, 2), ("twe", {"twe_nu": 0.001, "twe_lambda": 1.0}, 2500, 16, 2)]
+    items = []
+    for k, (kind, kw, L, ntr, nte) in enumerate(specs):
+        ds = synth.make_dataset(ntr, nte, L, 3, 7700 + k)
+        tr, te = synth.pack(ds.train), synth.pack(ds.test)
+        items.append((kind, kw, tr, te, eap.Nn1Task(gpu_params(eap, kind, **kw), eap.SeriesSet.from_packed(te),
+                                                    eap.SeriesSet.from_packed(tr))))
+    old = os.environ.get("EAP_MAP")
+    try:
+        for mapping in (None, "cta"):
+            if mapping:
+                os.environ["EAP_MAP"] = mapping
+            st = eap.eap_nn1_batch([t for *_, t in items], with_stats=True)
+            torch.cuda.synchronize()
+            assert st["dp_ms"] > 0
+            for kind, kw, tr, te, t in items:
+                i1, d1 = eap.eap_nn1(t.p, t.queries, t.refs)
+                assert np.array_equal(t.out_idx.cpu().numpy(), i1.cpu().numpy()), (kind, mapping)
+                assert np.array_equal(t.out_dist.cpu().numpy(), d1.cpu().numpy()), (kind, mapping)
+    finally:
+        if old is None:
+            os.environ.pop("EAP_MAP", None)
+        else:
+            os.environ["EAP_MAP"] = old
+    for kind, kw, tr, te, t in items:
+        D = O.cross(oracle_params(kind, **kw), te, tr)
+        check_nn(t.out_idx.cpu().numpy(), t.out_dist.cpu().numpy(), D)
