@@ -801,8 +801,9 @@ def _uneven_tasks(eap, synth):
 
 
 def workload_uneven_64(args):
-    """64 datasets (L 24..2048), CDTW+LB_Keogh2, ERP and TWE: one persistent
-    launch per step replayed from a CUDA graph, against one launch per query."""
+    """64 datasets (L 24..2048), CDTW+LB_Keogh2, ERP and TWE: one
+    eap_nn1_batch call per step (batched pre-passes, each task's DP on its
+    own kernel) replayed from a CUDA graph, against one launch per query."""
     import numpy as np
     import torch
 

@@ -42,7 +42,7 @@ using Clock = std::chrono::steady_clock;
 constexpr int kSlots = 8;                    // streams with a launch in flight
 constexpr int kBatchMaxQueries = 512;
 constexpr int64_t kBatchMaxFloats = 1 << 22; // query floats per launch (16 MiB)
-constexpr double kClassFactor = 4.0;         // a launch takes queries with up to this much the lead's work
+constexpr double kClassFactor = 2.0;         // a launch takes queries with up to this much the lead's work
 constexpr double kMaxWaitMs = 200.0;         // a query waiting this long leads the next launch
 
 struct RefSet {
