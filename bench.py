@@ -83,7 +83,7 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -114,7 +114,7 @@ class ClockSampler:
             os.unlink(self.path)
         except Exception:
             return out
-        sm, mx, reasons = [], [], set()
+        sm, mx, busy, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             r = [x.strip() for x in r]
@@ -125,12 +125,21 @@ class ClockSampler:
                 mx.append(float(r[2]))
             except ValueError:
                 continue
+            try:
+                if len(r) > 9 and float(r[9]) > 0:
+                    busy.append(float(r[1]))   # a sample taken while kernels were running
+            except ValueError:
+                pass
             for nm, v in zip(names, r[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if sm:
-            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                   "samples": len(sm)}
+            # The median under load: samples taken while the GPU was busy
+            # (host-side set-up of a workload leaves it idle at low clocks).
+            load = busy if busy else sm
+            out = {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm), "samples_under_load": len(busy),
+                   "sm_mhz_all_samples": statistics.median(sm)}
         return out
 
 
@@ -293,6 +302,8 @@ def main():
     ap.add_argument("--no-unpruned", action="store_true",
                     help="skip the unpruned (Base) DP block of the benchmark line")
     ap.add_argument("--unpruned-steps", type=int, default=2)
+    ap.add_argument("--stats-steps", type=int, default=3,
+                    help="untimed steps after the timed region for the per-distance statistics")
     ap.add_argument("--kinds", default=",".join(KIND_PARAMS),
                     help="subset of distances (profiling runs only; the benchmark is all six)")
     ap.add_argument("--n-test", type=int, default=N_TEST, help="test series per rank (profiling runs only)")
@@ -367,16 +378,27 @@ def main():
                 c["cells_effective"] += st["cells_effective"]
                 c["calls"] += 1
             return
-        for k in kinds:
-            _, _, st = eap.eap_nn1(params[k], Q, R, stream=stream, with_stats=True,
-                                   out_idx=out_idx[k], out_dist=out_dist[k])
-            if collect is not None:
+        if collect is not None:
+            # Per-distance statistics (DP time by the library's CUDA events,
+            # cell counters): one distance at a time, each call synchronised.
+            for k in kinds:
+                _, _, st = eap.eap_nn1(params[k], Q, R, stream=stream, with_stats=True,
+                                       out_idx=out_idx[k], out_dist=out_dist[k])
                 c = collect.setdefault(k, {"dp_ms": 0.0, "cells_computed": 0, "cells_effective": 0, "calls": 0})
                 c["dp_ms"] += st["dp_ms"]
                 c["cells_computed"] += st["cells_computed"]
                 c["cells_effective"] += st["cells_effective"]
                 c["calls"] += 1
+            return
+        # The timed step: the six 1-NN searches, each on its own stream forked
+        # from and joined to the step's stream, nothing synchronised on the host.
+        for k in kinds:
+            side[k].wait_stream(stream)
+            eap.eap_nn1(params[k], Q, R, stream=side[k], out_idx=out_idx[k], out_dist=out_dist[k])
+        for k in kinds:
+            stream.wait_stream(side[k])
 
+    side = {k: torch.cuda.Stream() for k in kinds}
     for _ in range(max(3, args.warmup)):
         step(None)
     torch.cuda.synchronize()
@@ -391,12 +413,16 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step(per)
+        step(None)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
     t_ms = e0.elapsed_time(e1)
+    # Per-distance breakdown, after the timed region (untimed steps).
+    for _ in range(max(1, args.stats_steps)):
+        step(per)
+    torch.cuda.synchronize()
     if world > 1:
         t = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -202,6 +202,22 @@ int eap_pairs(const eap_params* p, const eap_series_set* a, const eap_series_set
 int eap_lb_keogh(const eap_params* p, const eap_series_set* a, const eap_series_set* b,
                  const int32_t* ia, const int32_t* ib, float* out, int32_t n, void* cuda_stream);
 
+/* The lower-bound pass of the 1-NN search (Alg. 2; the lb-keogh2 cascade of
+ * Section 5.2), as eap_nn1 runs it ahead of the DP when p->lb is set:
+ *   out_lb[q * refs->count + c] = max(LB_Keogh(Q_q, C_c), LB_Keogh(C_c, Q_q))
+ * (only the first term when two_way = 0), each the textbook bound -- the
+ * envelope U/L of one series over |k - i| <= w bounds the points of the
+ * other, cost(c_i, U_i) above U, cost(c_i, L_i) below L -- with
+ * w = floor(ratio * L) (CDTW) or the whole series (DTW), and the distance's
+ * cost; multiplied by 1 - (4L + 16) 2^-24 so that float32 rounding never
+ * lifts it above the pair's float32 DP value.  Pairs of unequal length get 0.
+ *   out_lb  device float[queries->count * refs->count], row-major by query.
+ * p->kind must be EAP_DTW or EAP_CDTW (else EAP_EINVAL); p->prune and p->lb
+ * are not used.  Envelopes are stream-ordered scratch (8 bytes per element of
+ * each set); asynchronous on the stream. */
+int eap_lb_matrix(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t two_way,
+                  float* out_lb, void* cuda_stream);
+
 /* eap_pairs without any allocation.  (The paper has no counterpart: this is
  * a deployment variant of eap_pairs.)
  *

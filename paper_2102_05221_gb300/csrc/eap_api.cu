@@ -220,23 +220,90 @@ __global__ void lb_keogh_pairs_kernel(const SeriesDev A, const SeriesDev B, cons
 
 // Envelope of every series for LB_Keogh (Section 5.2): U[k] / Lo[k] = max /
 // min of x over |m - k| <= w, w the pair window of an equal-length pair.
-__global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict__ U, float* __restrict__ Lo) {
+// One block per series.  With `smem_len` > 0 (the launch's longest series,
+// 4 floats per point of shared memory) the van Herk / Gil-Werman form runs in
+// O(L): the series is cut into blocks of k = 2w + 1 points, each block keeps
+// running maxima / minima from its start (g) and from its end (h), and a
+// window [a, b] -- at most k points, so it spans at most two blocks -- is
+// max(h[a], g[b]); a window inside one block starts at the block (then g[b])
+// or ends at the series' end (then h[a]).  Max and min are exact, so the
+// result is the same as scanning each window.  Without shared memory each
+// point scans its window.
+__global__ void envelope_kernel(const SeriesDev S, KParams kp, float* __restrict__ U, float* __restrict__ Lo,
+                                int smem_len) {
+    extern __shared__ float env_sh[];
     const int s = blockIdx.x;
     const int L = S.len[s];
     const float* x = S.data + S.off[s];
+    float* u = U + S.off[s];
+    float* lo = Lo + S.off[s];
     int w = pair_window(kp, L, L);
     if (w > L) w = L;
+    if (smem_len > 0) {
+        const int k = 2 * w + 1;
+        float* gmax = env_sh;
+        float* hmax = gmax + smem_len;
+        float* gmin = hmax + smem_len;
+        float* hmin = gmin + smem_len;
+        const int nb = (L + k - 1) / k;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int a0 = b * k, a1 = min(L, a0 + k);
+            float m = -EAP_FINF, n = EAP_FINF;
+            for (int i = a0; i < a1; ++i) {
+                const float v = __ldg(x + i);
+                m = fmaxf(m, v);
+                n = fminf(n, v);
+                gmax[i] = m;
+                gmin[i] = n;
+            }
+            m = -EAP_FINF;
+            n = EAP_FINF;
+            for (int i = a1 - 1; i >= a0; --i) {
+                const float v = __ldg(x + i);
+                m = fmaxf(m, v);
+                n = fminf(n, v);
+                hmax[i] = m;
+                hmin[i] = n;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const int a = max(0, i - w), b = min(L - 1, i + w);
+            float mu, ml;
+            if (a / k != b / k) {
+                mu = fmaxf(hmax[a], gmax[b]);
+                ml = fminf(hmin[a], gmin[b]);
+            } else if (a % k == 0) {
+                mu = gmax[b];
+                ml = gmin[b];
+            } else {
+                mu = hmax[a];
+                ml = hmin[a];
+            }
+            u[i] = mu;
+            lo[i] = ml;
+        }
+        return;
+    }
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
-        float u = -EAP_FINF, lo = EAP_FINF;
+        float uu = -EAP_FINF, ll = EAP_FINF;
         const int a = max(0, k - w), b = min(L - 1, k + w);
         for (int m = a; m <= b; ++m) {
             const float v = __ldg(x + m);
-            u = fmaxf(u, v);
-            lo = fminf(lo, v);
+            uu = fmaxf(uu, v);
+            ll = fminf(ll, v);
         }
-        U[S.off[s] + k] = u;
-        Lo[S.off[s] + k] = lo;
+        u[k] = uu;
+        lo[k] = ll;
     }
+}
+
+// Envelopes of every series of a set (max_len: its longest series).
+void launch_envelope(const SeriesDev& S, const KParams& ke, int max_len, float* U, float* Lo, cudaStream_t st) {
+    if (S.n <= 0) return;
+    const size_t smem = (size_t)4 * max_len * sizeof(float);
+    const bool fast = smem <= 48 * 1024;
+    envelope_kernel<<<S.n, 128, fast ? smem : 0, st>>>(S, ke, U, Lo, fast ? max_len : 0);
 }
 
 // Lower bound of every (query, candidate) pair, [q][c]: LB_Keogh(Q, C) (the
@@ -869,8 +936,8 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
         KParams ke = make_kparams(p);
         ke.windowed = 1;
         if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }   // DTW: the whole series
-        envelope_kernel<<<nq, 128, 0, st>>>(dev_set(qs, nullptr), ke, L.qU, L.qL);
-        if (use_lb2) envelope_kernel<<<nr, 128, 0, st>>>(dev_set(rs, nullptr), ke, L.rU, L.rL);
+        launch_envelope(dev_set(qs, nullptr), ke, mq, L.qU, L.qL, st);
+        if (use_lb2) launch_envelope(dev_set(rs, nullptr), ke, mr, L.rU, L.rL, st);
         launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), L.qU, L.qL, L.rU, L.rL, cost, use_lb2 ? 1 : 0,
                          L.lb, st);
         if ((e = (int)cudaGetLastError())) { sc.release(); return cuda_status(e); }
@@ -971,6 +1038,44 @@ int eap_nn1_keys(const eap_params* p, const eap_series_set* queries, const eap_s
     if (index_offset < 0 || index_offset + (int64_t)refs->count >= (int64_t)kNoIndex) return EAP_EINVAL;
     return nn1_impl(p, queries, refs, nullptr, nullptr, (cudaStream_t)cuda_stream, opt_stats, nullptr,
                     (unsigned long long*)out_keys, (long long)index_offset);
+}
+
+int eap_lb_matrix(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t two_way,
+                  float* out_lb, void* cuda_stream) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (two_way != 0 && two_way != 1) return EAP_EINVAL;
+    return with_derivative(p, queries, refs, st, [&](const eap_params* q, const eap_series_set* qs,
+                                                     const eap_series_set* rs) {
+        int rc = validate_params(q);
+        if (rc) return rc;
+        int mq = 0, mr = 0;
+        if ((rc = validate_set(qs, &mq)) || (rc = validate_set(rs, &mr))) return rc;
+        if (q->kind != EAP_DTW && q->kind != EAP_CDTW) return EAP_EINVAL;
+        if (qs->count == 0 || rs->count == 0) return EAP_OK;
+        if (!out_lb) return EAP_EINVAL;
+        Scratch sc;
+        auto layout = [&]() {
+            struct { float *qU, *qL, *rU, *rL; } L;
+            L.qU = (float*)sc.take(sizeof(float) * (size_t)qs->data_len);
+            L.qL = (float*)sc.take(sizeof(float) * (size_t)qs->data_len);
+            L.rU = two_way ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
+            L.rL = two_way ? (float*)sc.take(sizeof(float) * (size_t)rs->data_len) : nullptr;
+            return L;
+        };
+        layout();
+        if ((rc = sc.alloc(st))) return rc;
+        const auto L = layout();
+        KParams ke = make_kparams(q);
+        ke.windowed = 1;
+        if (q->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }   // DTW: the whole series
+        launch_envelope(dev_set(qs, nullptr), ke, mq, L.qU, L.qL, st);
+        if (two_way) launch_envelope(dev_set(rs, nullptr), ke, mr, L.rU, L.rL, st);
+        launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), L.qU, L.qL, L.rU, L.rL, resolve_cost(q),
+                         two_way, out_lb, st);
+        const int e = (int)cudaGetLastError();
+        sc.release();
+        return cuda_status(e);
+    });
 }
 
 int eap_keys_unpack(const uint64_t* keys, int32_t n, int32_t* out_idx, float* out_dist, void* cuda_stream) {
@@ -1510,8 +1615,11 @@ void launch_lb(const eap_params* p, const eap_series_set* qs, const eap_series_s
     KParams ke = make_kparams(p);
     ke.windowed = 1;
     if (p->kind == EAP_DTW) { ke.window_abs = -1; ke.window_ratio = -1.f; }
-    envelope_kernel<<<qs->count, 128, 0, st>>>(dev_set(qs, nullptr), ke, qU, qL);
-    if (two_way) envelope_kernel<<<rs->count, 128, 0, st>>>(dev_set(rs, nullptr), ke, rU, rL);
+    int mq = 0, mr = 0;
+    for (int i = 0; i < qs->count; ++i) mq = std::max(mq, (int)qs->h_lengths[i]);
+    for (int i = 0; i < rs->count; ++i) mr = std::max(mr, (int)rs->h_lengths[i]);
+    launch_envelope(dev_set(qs, nullptr), ke, mq, qU, qL, st);
+    if (two_way) launch_envelope(dev_set(rs, nullptr), ke, mr, rU, rL, st);
     launch_lb_matrix(dev_set(qs, nullptr), dev_set(rs, nullptr), qU, qL, rU, rL, resolve_cost(p), two_way, lb, st);
 }
 KParams kparams_of(const eap_params* p) { return make_kparams(p); }

@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
         lib.eap_nn1_keys.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), ctypes.c_int64, vp, vp,
                                      P(eap_stats)]
         lib.eap_keys_unpack.argtypes = [vp, i32, vp, vp, vp]
+        lib.eap_lb_matrix.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), i32, vp, vp]
         if hasattr(lib, "eap_serve_create"):
             lib.eap_serve_create.argtypes = [P(eap_serve_config), P(ctypes.c_int)]
             lib.eap_serve_create.restype = vp
@@ -101,7 +102,7 @@ def load(build_if_missing: bool = True):
             lib.eap_serve_destroy.argtypes = [vp]
         lib.eap_subseq.argtypes = [P(eap_params), vp, ctypes.c_int64, P(eap_series_set), vp, vp, vp, P(eap_stats)]
         for name in ("eap_nn1", "eap_nn1_host", "eap_pairwise", "eap_pairs", "eap_lb_keogh", "eap_subseq",
-                     "eap_nn1_keys", "eap_keys_unpack"):
+                     "eap_nn1_keys", "eap_keys_unpack", "eap_lb_matrix"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -219,6 +220,19 @@ def eap_nn1_keys(p: eap_params, queries: SeriesSet, refs: SeriesSet, index_offse
                           ctypes.byref(st) if with_stats else None)
     _check(rc, "eap_nn1_keys")
     return (keys, st.as_dict()) if with_stats else keys
+
+
+def eap_lb_matrix(p: eap_params, queries: SeriesSet, refs: SeriesSet, two_way: bool = True, stream=None):
+    """The 1-NN search's lower-bound pass: [queries x refs] float32 tensor of
+    max(LB_Keogh(Q, C), LB_Keogh(C, Q)) (first term only without two_way)."""
+    torch = _torch()
+    lib = load()
+    out = torch.empty((queries.count, refs.count), dtype=torch.float32, device=queries.data.device)
+    qs, rs = queries.struct(), refs.struct()
+    rc = lib.eap_lb_matrix(ctypes.byref(p), ctypes.byref(qs), ctypes.byref(rs), int(bool(two_way)),
+                           ctypes.c_void_p(out.data_ptr() if out.numel() else 0), _stream_ptr(stream))
+    _check(rc, "eap_lb_matrix")
+    return out
 
 
 def eap_keys_unpack(keys, stream=None, out_idx=None, out_dist=None):
