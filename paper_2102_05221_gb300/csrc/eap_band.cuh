@@ -63,6 +63,7 @@ namespace eapd {
 #define EAP_BAND_MINB 0
 #endif
 
+
 template <int G>
 __device__ __forceinline__ unsigned band_group_mask(int lane) {
     return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -343,7 +344,10 @@ __global__ void __launch_bounds__(kThreads, EAP_BAND_MINB) band_dp_kernel(const 
 #pragma unroll
             for (int k = 0; k < U; ++k) step(s + k, BoolC<false>{});
         } else {
-#pragma unroll
+            // Predicated rounds (pair starts and ends) stay rolled: explicit
+            // register moves for the column shift in a minority of rounds buy
+            // half the kernel's code (instruction-cache misses otherwise).
+#pragma unroll 1
             for (int k = 0; k < U; ++k) step(s + k, BoolC<true>{});
         }
         s += U;
