@@ -312,51 +312,53 @@ void launch_envelope(const SeriesDev& S, const KParams& ke, int max_len, float* 
 // Pairs of unequal length get 0.  The bound is shrunk by 1 - (4L + 16) 2^-24
 // so float rounding can never lift it above the float32 DP value of the pair.
 //
-// Tiled like a matrix product: a block owns kLbTq queries x kLbTc candidates
-// and walks the points in chunks of kLbK, staging the chunk of every series
-// of the tile (query: U, L, x; candidate: y, U, L) in shared memory once, so
-// each candidate chunk is read from memory once per query tile instead of
-// once per query.  Thread (ty, tx) of the 16 x 16 block accumulates the 4 x 4
-// pairs (ty + 16a, tx + 16b).  Per point and direction, the textbook case
-// split "cost(c_i, U_i) if c_i > U_i, cost(c_i, L_i) if c_i < L_i, else 0" is
-// cost(c_i, clamp(c_i, L_i, U_i)): the same difference, rounded the same way.
-// Points past a series' end are padded so that they add 0.
-constexpr int kLbTq = 64, kLbTc = 64, kLbK = 32;
+// Tiled like a matrix product: a block owns TQ queries x TC candidates and
+// walks the points in chunks of kLbK, staging the chunk of every series of
+// the tile (query: U, L, x; candidate: y, U, L) in shared memory once, so each
+// candidate chunk is read from memory once per query tile instead of once per
+// query.  Thread (ty, tx) of the (TQ/4) x (TC/4) block accumulates the 4 x 4
+// pairs (ty + (TQ/4) a, tx + (TC/4) b).  Per point and direction, the textbook
+// case split "cost(c_i, U_i) if c_i > U_i, cost(c_i, L_i) if c_i < L_i, else
+// 0" is cost(c_i, clamp(c_i, L_i, U_i)): the same difference, rounded the same
+// way.  Points past a series' end are padded so that they add 0.
+constexpr int kLbK = 32;
 constexpr int kLbStride = kLbK + 1;   // shared-memory row pitch (conflict-free column reads)
-constexpr size_t kLbSmemBytes = sizeof(float) * 6 * 64 * kLbStride;
 
 __device__ __forceinline__ float lb_term(float y, float lo, float up, int cost, float acc) {
     const float d = __fsub_rn(y, fminf(fmaxf(y, lo), up));
     return cost == 0 ? __fmaf_rn(d, d, acc) : __fadd_rn(acc, fabsf(d));
 }
 
-__global__ void __launch_bounds__(256) lb_matrix_kernel(const SeriesDev Q, const SeriesDev R,
-                                                        const float* __restrict__ qU, const float* __restrict__ qL,
-                                                        const float* __restrict__ rU, const float* __restrict__ rL,
-                                                        int cost, int two_way, float* __restrict__ lb) {
+template <int TQ, int TC>
+constexpr size_t lb_smem_bytes() { return sizeof(float) * 3 * (TQ + TC) * kLbStride; }
+
+template <int TQ, int TC>
+__global__ void __launch_bounds__((TQ / 4) * (TC / 4)) lb_matrix_kernel(
+        const SeriesDev Q, const SeriesDev R, const float* __restrict__ qU, const float* __restrict__ qL,
+        const float* __restrict__ rU, const float* __restrict__ rL, int cost, int two_way, float* __restrict__ lb) {
+    constexpr int NX = TC / 4, NY = TQ / 4, NT = NX * NY;
     extern __shared__ float lbs[];
-    float* sqU = lbs;                          // [64][kLbStride] per array
-    float* sqL = sqU + 64 * kLbStride;
-    float* sqx = sqL + 64 * kLbStride;
-    float* scy = sqx + 64 * kLbStride;
-    float* scU = scy + 64 * kLbStride;
-    float* scL = scU + 64 * kLbStride;
-    __shared__ int s_len[kLbTq + kLbTc];
-    __shared__ int64_t s_off[kLbTq + kLbTc];
+    float* sqU = lbs;                          // [TQ][kLbStride]
+    float* sqL = sqU + TQ * kLbStride;
+    float* sqx = sqL + TQ * kLbStride;
+    float* scy = sqx + TQ * kLbStride;         // [TC][kLbStride]
+    float* scU = scy + TC * kLbStride;
+    float* scL = scU + TC * kLbStride;
+    __shared__ int s_len[TQ + TC];
+    __shared__ int64_t s_off[TQ + TC];
     __shared__ int s_max;
-    const int q0 = blockIdx.y * kLbTq, c0 = blockIdx.x * kLbTc;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int q0 = blockIdx.y * TQ, c0 = blockIdx.x * TC;
+    const int tx = threadIdx.x % NX, ty = threadIdx.x / NX;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    if (threadIdx.x < kLbTq + kLbTc) {
-        const int k = threadIdx.x;
+    for (int k = threadIdx.x; k < TQ + TC; k += NT) {
         int len = 0;
         int64_t off = 0;
-        if (k < kLbTq) {
+        if (k < TQ) {
             if (q0 + k < Q.n) { len = Q.len[q0 + k]; off = Q.off[q0 + k]; }
-        } else if (c0 + k - kLbTq < R.n) {
-            len = R.len[c0 + k - kLbTq];
-            off = R.off[c0 + k - kLbTq];
+        } else if (c0 + k - TQ < R.n) {
+            len = R.len[c0 + k - TQ];
+            off = R.off[c0 + k - TQ];
         }
         s_len[k] = len;
         s_off[k] = off;
@@ -369,19 +371,20 @@ __global__ void __launch_bounds__(256) lb_matrix_kernel(const SeriesDev Q, const
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) { acc1[a][b] = 0.f; acc2[a][b] = 0.f; }
+    const int warp = threadIdx.x >> 5, nwarps = NT / 32;
     for (int i0 = 0; i0 < maxlen; i0 += kLbK) {
-        // Stage the chunk: 128 series x 32 points, one warp per series row at a time.
-        for (int r = threadIdx.x >> 5; r < kLbTq + kLbTc; r += 8) {
-            const int i = i0 + (threadIdx.x & 31);
+        // Stage the chunk: TQ + TC series x 32 points, one warp per series row at a time.
+        for (int r = warp; r < TQ + TC; r += nwarps) {
+            const int col = threadIdx.x & 31;
+            const int i = i0 + col;
             const bool in = i < s_len[r];
             const int64_t o = s_off[r] + i;
-            const int col = threadIdx.x & 31;
-            if (r < kLbTq) {
+            if (r < TQ) {
                 sqU[r * kLbStride + col] = in ? __ldg(qU + o) : EAP_FINF;
                 sqL[r * kLbStride + col] = in ? __ldg(qL + o) : -EAP_FINF;
                 if (two_way) sqx[r * kLbStride + col] = in ? __ldg(Q.data + o) : 0.f;
             } else {
-                const int rc = r - kLbTq;
+                const int rc = r - TQ;
                 scy[rc * kLbStride + col] = in ? __ldg(R.data + o) : 0.f;
                 if (two_way) {
                     scU[rc * kLbStride + col] = in ? __ldg(rU + o) : EAP_FINF;
@@ -395,14 +398,14 @@ __global__ void __launch_bounds__(256) lb_matrix_kernel(const SeriesDev Q, const
             float u[4], l[4], x[4], y[4], cu[4], cl[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                u[a] = sqU[(ty + 16 * a) * kLbStride + k];
-                l[a] = sqL[(ty + 16 * a) * kLbStride + k];
-                if (two_way) x[a] = sqx[(ty + 16 * a) * kLbStride + k];
+                u[a] = sqU[(ty + NY * a) * kLbStride + k];
+                l[a] = sqL[(ty + NY * a) * kLbStride + k];
+                if (two_way) x[a] = sqx[(ty + NY * a) * kLbStride + k];
             }
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                y[b] = scy[(tx + 16 * b) * kLbStride + k];
-                if (two_way) { cu[b] = scU[(tx + 16 * b) * kLbStride + k]; cl[b] = scL[(tx + 16 * b) * kLbStride + k]; }
+                y[b] = scy[(tx + NX * b) * kLbStride + k];
+                if (two_way) { cu[b] = scU[(tx + NX * b) * kLbStride + k]; cl[b] = scL[(tx + NX * b) * kLbStride + k]; }
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -416,27 +419,36 @@ __global__ void __launch_bounds__(256) lb_matrix_kernel(const SeriesDev Q, const
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int qa = ty + 16 * a, q = q0 + qa;
+        const int qa = ty + NY * a, q = q0 + qa;
         if (q >= Q.n) continue;
         const int Lq = s_len[qa];
         const float shrink = 1.0f - (float)(4 * Lq + 16) * 5.9604645e-8f;   // 1 - (4L + 16) 2^-24
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int cb = tx + 16 * b, c = c0 + cb;
+            const int cb = tx + NX * b, c = c0 + cb;
             if (c >= R.n) continue;
-            const float v = s_len[kLbTq + cb] == Lq ? __fmul_rn(fmaxf(acc1[a][b], acc2[a][b]), shrink) : 0.f;
+            const float v = s_len[TQ + cb] == Lq ? __fmul_rn(fmaxf(acc1[a][b], acc2[a][b]), shrink) : 0.f;
             lb[(size_t)q * R.n + c] = v;
         }
     }
 }
 
+template <int TQ, int TC>
+void lb_launch(const SeriesDev& Q, const SeriesDev& R, const float* qU, const float* qL, const float* rU,
+               const float* rL, int cost, int two_way, float* lb, cudaStream_t st) {
+    const dim3 grid((unsigned)((R.n + TC - 1) / TC), (unsigned)((Q.n + TQ - 1) / TQ));
+    lb_matrix_kernel<TQ, TC><<<grid, (TQ / 4) * (TC / 4), lb_smem_bytes<TQ, TC>(), st>>>(Q, R, qU, qL, rU, rL, cost,
+                                                                                         two_way, lb);
+}
+
 void launch_lb_matrix(const SeriesDev& Q, const SeriesDev& R, const float* qU, const float* qL, const float* rU,
                       const float* rL, int cost, int two_way, float* lb, cudaStream_t st) {
     if (Q.n <= 0 || R.n <= 0) return;
-    // Opt-in shared memory above 48 KB (a property of the kernel on the current device).
-    cudaFuncSetAttribute(lb_matrix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLbSmemBytes);
-    const dim3 grid((unsigned)((R.n + kLbTc - 1) / kLbTc), (unsigned)((Q.n + kLbTq - 1) / kLbTq));
-    lb_matrix_kernel<<<grid, 256, kLbSmemBytes, st>>>(Q, R, qU, qL, rU, rL, cost, two_way, lb);
+    // 64 x 64 tiles: smaller ones (better wave fill for few queries) measured
+    // slower -- less reuse of each staged chunk, fewer warps per SM.
+    cudaFuncSetAttribute(lb_matrix_kernel<64, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)lb_smem_bytes<64, 64>());
+    lb_launch<64, 64>(Q, R, qU, qL, rU, rL, cost, two_way, lb, st);
 }
 
 // ---------------------------------------------------------------------------
