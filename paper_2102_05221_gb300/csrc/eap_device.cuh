@@ -161,6 +161,9 @@ struct FDtw {
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
     __device__ static Row row(float s, float, const KParams&, const float*) { return {s, nullptr}; }
+    // Constants enough for the diagonal candidate alone (the diagonal-path bound).
+    __device__ static Col col_diag(float t, float tp, const KParams& kp) { return col(t, tp, kp); }
+    __device__ static Row row_diag(float s, float sp, const KParams& kp, const float* wt) { return row(s, sp, kp, wt); }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams&) {
         const float m = min3f(dg, tp, lf);
@@ -210,6 +213,8 @@ struct FWdtw {
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
     __device__ static Row row(float s, float, const KParams&, const float* wt) { return {s, wt}; }
+    __device__ static Col col_diag(float t, float tp, const KParams& kp) { return col(t, tp, kp); }
+    __device__ static Row row_diag(float s, float sp, const KParams& kp, const float* wt) { return row(s, sp, kp, wt); }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int dij, float,
                                  const KParams&) {
         const float m = min3f(dg, tp, lf);
@@ -268,6 +273,12 @@ struct FErp {
     __device__ static Row row(float s, float, const KParams& kp, const float*) {
         const float cs = pcost<COST>(s, kp.erp_gap);
         return {make_float2(s, s), make_float2(cs, cs)};
+    }
+    // On the diagonal path the vertical and horizontal candidates add to +inf:
+    // their gap costs are not needed (0 keeps those candidates +inf).
+    __device__ static Col col_diag(float t, float, const KParams&) { return {t, 0.f}; }
+    __device__ static Row row_diag(float s, float, const KParams&, const float*) {
+        return {make_float2(s, s), make_float2(0.f, 0.f)};
     }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams&) {
@@ -341,6 +352,10 @@ struct FMsm {
         const float e = __fsub_rn(sprev, s);
         return {make_float2(s, s), e != 0.f ? __frcp_rn(e) : 0.f, fabsf(e)};
     }
+    // On the diagonal path the split/merge candidates add to +inf: no
+    // reciprocals needed (0 makes those costs c, finite, and the candidates +inf).
+    __device__ static Col col_diag(float t, float, const KParams&) { return {t, 0.f, 0.f}; }
+    __device__ static Row row_diag(float s, float, const KParams&, const float*) { return {make_float2(s, s), 0.f, 0.f}; }
     __device__ static float cell(float dg, float tp, float lf, const Row& r, const Col& c, int, float,
                                  const KParams& kp) {
         const float f = __fsub_rn(c.t, r.s2.x);                                // t_j - s_i
@@ -415,6 +430,13 @@ struct FTwe {
     __device__ static Row row(float s, float sprev, const KParams& kp, const float*) {
         const float ga = __fadd_rn(__fadd_rn(pcost<COST>(s, sprev), kp.twe_nu), kp.twe_lambda);
         return {s, sprev, make_float2(ga, ga)};
+    }
+    // On the diagonal path the deletion candidates add to +inf: their costs
+    // are not needed (0 keeps them +inf); the match cost uses s, t and their
+    // predecessors as in the DP.
+    __device__ static Col col_diag(float t, float tprev, const KParams&) { return {t, tprev, 0.f}; }
+    __device__ static Row row_diag(float s, float sprev, const KParams&, const float*) {
+        return {s, sprev, make_float2(0.f, 0.f)};
     }
     // 2 nu |i - j| for a cell with i - j = d (an integer, or its exact float).
     __device__ static float pen(const KParams& kp, int d) { return __fmul_rn(kp.twe_nu2, (float)abs(d)); }
@@ -843,8 +865,8 @@ __device__ float diag_path_cost_b(const PairIn& in, const float* Bs, const KPara
     float sp = 0.f, tp = 0.f;
     for (int k = 1; k <= m; ++k) {
         const float s = __ldg(in.A + k - 1), t = Bs[k - 1];
-        const typename F::Row rc = F::row(s, sp, kp, in.wt);
-        const typename F::Col c = F::col(t, tp, kp);
+        const typename F::Row rc = F::row_diag(s, sp, kp, in.wt);
+        const typename F::Col c = F::col_diag(t, tp, kp);
         acc = F::cell(acc, EAP_FINF, EAP_FINF, rc, c, 0, 0.f, kp);
         sp = s; tp = t;
     }
@@ -877,8 +899,8 @@ __device__ float diag_path_cost(const PairIn& in, const KParams& kp) {
     float sp = 0.f, tp = 0.f;
     for (int k = 1; k <= m; ++k) {
         const float s = __ldg(in.A + k - 1), t = __ldg(in.B + k - 1);
-        const typename F::Row rc = F::row(s, sp, kp, in.wt);
-        const typename F::Col c = F::col(t, tp, kp);
+        const typename F::Row rc = F::row_diag(s, sp, kp, in.wt);
+        const typename F::Col c = F::col_diag(t, tp, kp);
         acc = F::cell(acc, EAP_FINF, EAP_FINF, rc, c, 0, 0.f, kp);
         sp = s; tp = t;
     }
