@@ -15,10 +15,15 @@
 // group-local collectives only), (2) the warp re-converges and runs U
 // wavefront steps in lock-step, every lane predicated by its own group's
 // state, (3) one ballot gives each group its frontier vote, and groups whose
-// panel ended process its end (divergent).  The arithmetic of a cell, the
-// pruning rules and the results are those of warp_pair in the EAPruned mode
-// (with DPJob::no_cut, of the Base mode: the cut-off is +inf, so every panel
-// runs to its last row and nothing is abandoned).
+// panel ended process its end (divergent).  Per round a group also refreshes
+// its cut-off from the query's best-so-far (a load issued one vote earlier,
+// so the warp never waits for it), and the shared-memory boundary column is
+// never cleared in full: rows past those the pair has written are set to
+// +inf in blocks, ahead of the rows the group's first lane reads.  The
+// arithmetic of a cell, the pruning rules and the results are those of
+// warp_pair in the EAPruned mode (with DPJob::no_cut, of the Base mode: the
+// cut-off is +inf, so every panel runs to its last row and nothing is
+// abandoned).
 #pragma once
 
 #include "eap_device.cuh"
@@ -45,6 +50,8 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
     constexpr int P = G * W;                 // columns per panel
     constexpr int NG = 32 / G;               // groups per warp
     constexpr int U = kGroupRounds * (W + 1);   // steps per round (the strip registers rotate back every W + 1)
+    constexpr int kFillRows = 64;            // boundary rows set to +inf at a time (>= U)
+    static_assert(U <= kFillRows && kFillRows % G == 0, "boundary fill");
     enum { kNeedPair = 0, kNeedPanel = 1, kStep = 2, kDone = 3 };
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31;
@@ -59,6 +66,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
     // counters belong to the group's first lane.
     struct Cold {
         PairIn in;
+        const unsigned* cut_hi;   // high word (the distance) of the query's best-so-far, or null
         unsigned long long item;
         int ai, bi, npan, p, blo, cf, cl;
         bool last;
@@ -71,7 +79,9 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
 
     int state = kNeedPair;
     float cut = EAP_FINF;
+    unsigned cut_next = 0x7f800000u;   // best-so-far read at the last vote, taken at the next one
     int bhi = 0;
+    int vhi = 0;   // rows 1..vhi of the boundary column hold this pair's values (see begin_panel)
     // What a wavefront step reads of the pair.
     const float4* rp = nullptr;   // packed row constants (F::kPacked)
     const float* Ar = nullptr;    // row series (rows computed in place)
@@ -157,6 +167,8 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         in.w = pair_window(kp, in.La, in.Lb);
         in.cut = c;
         gc.in = in;
+        gc.cut_hi = cut_src ? reinterpret_cast<const unsigned*>(cut_src) + 1 : nullptr;
+        cut_next = 0x7f800000u;
         gc.item = item;
         gc.ai = ai;
         gc.bi = bi;
@@ -183,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             }
             if (live > 0) { blo = 1; bhi = live; }   // the border increases: live rows are a prefix
         }
+        vhi = F::kBorders ? min(in.La, in.w + 1) : 0;
         gc.blo = blo;
         __syncwarp(gmask);
         state = kNeedPanel;
@@ -198,12 +211,6 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         gc.cf = cf;
         gc.cl = cl;
         gc.last = last;
-        if (in.cut_src) {
-            unsigned long long cv = 0;
-            if (gl == 0) cv = *(volatile const unsigned long long*)in.cut_src;
-            cv = __shfl_sync(gmask, cv, 0, G);
-            cut = fminf(cut, __uint_as_float((unsigned)(cv >> 32)));
-        }
         const bool top_live = hborder<F>(in, cf - 1) <= cut;
         if (!top_live && blo > bhi) { finish_pair(EAP_FINF, true); return; }
         r0 = top_live ? 1 : blo;
@@ -214,12 +221,20 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             __syncwarp(gmask);   // every lane has read p and blo
             gc.blo = 1;
             bhi = 0;
+            vhi = 0;          // the skipped panel's cells are all outside the window
             gc.p = p + 1;
             return;   // still kNeedPanel
         }
-        for (int r = r0 + gl; r <= r1; r += G)
-            if (r < blo || r > bhi) bnd[r] = EAP_FINF;
-        __syncwarp(gmask);
+        // The boundary column is not cleared: its rows r0 - 1 .. vhi hold this
+        // pair's values of column cf - 1 (rows the previous panel computed, or
+        // rows it treated as dead, whose stored value is then above the
+        // cut-off or +inf), and the rows past vhi are set to +inf one round
+        // ahead of the group's first lane (fill_boundary).  A value above the
+        // cut-off in place of +inf changes no value at or below the cut-off.
+        if (r0 - 1 > vhi) {
+            if (gl == 0) bnd[r0 - 1] = EAP_FINF;
+            vhi = r0 - 1;
+        }
         c0 = cf + gl * W;
 #pragma unroll
         for (int u = 0; u < W; ++u) {
@@ -287,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             hi = max(hi, __shfl_xor_sync(gmask, hi, o, G));
         }
         if (hi < 0) { gc.blo = 1; bhi = 0; } else { gc.blo = lo; bhi = hi; }
+        vhi = max(wlast, r0 - 1);   // the next panel reads rows from r0 - 1 on
         gc.p = p + 1;
         __syncwarp(gmask);
         state = kNeedPanel;
@@ -299,6 +315,8 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         constexpr bool kCheck = decltype(check)::value;
         const int row = r0 + tt - gl;
         const bool act = kCheck ? (state == kStep && row >= r0 && row <= r1) : true;
+        // Every lane loads (the first lane's value is used) into a register
+        // of its own, independent of the shuffle's result.
         const float bv = act ? bnd[row] : EAP_FINF;
         float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1, G);
         if (gl == 0) x = bv;
@@ -326,6 +344,16 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
             if (state == kNeedPair) begin_pair();
             else begin_panel();
         }
+        // fill_boundary: +inf into the rows of the boundary column that the
+        // group's first lane reads this round and no panel of the pair wrote.
+        if (state == kStep && min(r0 + t + U - 1, r1) > vhi) {
+#pragma unroll
+            for (int k = 0; k < kFillRows / G; ++k) {
+                const int r = vhi + 1 + gl + k * G;
+                if (r <= r1) bnd[r] = EAP_FINF;
+            }
+            vhi = min(vhi + kFillRows, r1);
+        }
         __syncwarp();
         if (__ballot_sync(EAP_FULL, state == kStep) == 0u) break;   // every group is done
         // (2) U lock-step wavefront steps; unpredicated when every group is
@@ -343,6 +371,11 @@ __global__ void __launch_bounds__(kThreads, (group_min_blocks<F, W>())) group_dp
         // unread boundary rows) is above the cut-off.
         bool dead = true;
         if (state == kStep) {
+            // The best-so-far read at the previous vote (its load had a round
+            // to complete) tightens the cut-off; the next read starts now.
+            cut = fminf(cut, __uint_as_float(cut_next));
+            const unsigned* ch = gc.cut_hi;
+            if (ch) cut_next = *(volatile const unsigned*)ch;
             const int row = r0 + t + U - 1 - gl;
             if (row <= r1 && !lane_out) {
                 float m = dg;
