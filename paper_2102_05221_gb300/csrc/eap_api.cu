@@ -616,6 +616,25 @@ int choose_w(int kind, int cost, int max_cols, int prune) {
     return 5;
 }
 
+// Strip width of the CTA-per-pair mapping: EAP_W, else the autotuner's width
+// for the length bucket, else 8.  Measured on 16 x 200 1-NN at L = 8192 with
+// the CTA kernel: W = 8 against 4, DTW 26.1 -> 16.5 ms, MSM 97.1 -> 75.0 ms
+// (TWE already ran at 8); the per-step work of the CTA wavefront (boundary
+// read and write, row constants, shuffle) is spread over twice the cells.
+int choose_w_cta(int kind, int cost, int max_cols, int prune) {
+    const char* e = std::getenv("EAP_W");
+    if (e) {
+        const int w = std::atoi(e);
+        if (w == 4 || w == 5 || w == 8 || w == 16) return w;
+    }
+    if (prune == kPmPruned && kind >= 0 && kind < 6 && (cost == 0 || cost == 1)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        const int t = g_tune[kind][cost][length_bucket(max_cols)];
+        if (t) return t;
+    }
+    return 8;
+}
+
 // Lanes per pair for the EAPruned DP: 8 or 16 (group_dp_kernel, several pairs
 // per warp) or 0 (a warp per pair).  EAP_G overrides (8, 16, or 32 = warp).
 // Groups keep one boundary column per group in shared memory, so they are
@@ -931,7 +950,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.max_cols = mr;
     c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
     choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w(p->kind, cost, mr, c.prune); c.group = 0; }
+    if (c.cta) { c.W = choose_w_cta(p->kind, cost, mr, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g, &c.band_exact);
     c.stream = st;
     c.ub = d_ub;
@@ -1253,6 +1272,7 @@ int pairwise_core(const eap_params* p, const eap_series_set* set, float* out_mat
         c.max_cols = mx;
         c.cta = choose_cta(p->kind, cost, mx, mx, c.prune);
         c.group = c.cta ? 0 : choose_group(p->kind, cost, mx, mx, c.prune, c.W);
+        if (c.cta) c.W = choose_w_cta(p->kind, cost, mx, 0);
         choose_band(p->kind, c.prune, c.kp, set_min_len(set), mx, &c.band, &c.band_g, &c.band_exact);
         c.stream = st;
         c.ub = L.ub;
@@ -1345,7 +1365,7 @@ int pairs_core(const eap_params* p, const eap_series_set* a, const eap_series_se
     c.max_cols = mb;
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
+    if (c.cta) { c.W = choose_w_cta(p->kind, cost, mb, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g, &c.band_exact);
     c.stream = st;
     DpTimer tm(opt_stats != nullptr);
@@ -1517,7 +1537,7 @@ extern "C" int eap_pairs_noalloc(const eap_params* p, const eap_series_set* a, c
     // (the autotuned map or the default), else warp groups or band.
     c.cta = choose_cta(p->kind, cost, ma, mb, c.prune);
     choose_w_group(p->kind, cost, ma, mb, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w(p->kind, cost, mb, c.prune); c.group = 0; }
+    if (c.cta) { c.W = choose_w_cta(p->kind, cost, mb, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(a), set_min_len(b)), std::max(ma, mb), &c.band, &c.band_g, &c.band_exact);
     c.sms = sms;
     c.max_rows = ma;
@@ -1573,6 +1593,7 @@ int pick_w(int kind, int cost, int max_cols, int prune) { return choose_w(kind, 
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
     return choose_cta(kind, cost, max_rows, max_cols, prune);
 }
+int pick_w_cta(int kind, int cost, int max_cols, int prune) { return choose_w_cta(kind, cost, max_cols, prune); }
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W) {
     return choose_group(kind, cost, max_rows, max_cols, prune, W);
 }
@@ -1671,7 +1692,7 @@ int nn1_dp_launch(const eap_params* p, const eap_series_set* qs, const eap_serie
     c.max_cols = max_cols;
     c.cta = choose_cta(p->kind, cost, max_rows, max_cols, c.prune);
     choose_w_group(p->kind, cost, max_rows, max_cols, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w(p->kind, cost, max_cols, c.prune); c.group = 0; }
+    if (c.cta) { c.W = choose_w_cta(p->kind, cost, max_cols, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(max_rows, max_cols),
                 &c.band, &c.band_g, &c.band_exact);
     c.stream = st;

@@ -58,6 +58,8 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int La = in.La, Lb = in.Lb, w = in.w;
     constexpr int P = 32 * W;
+    constexpr int kCtaChunk = kTick / W;   // unrolled steps per chunk (16 at W = 4, 8 at W = 8)
+    static_assert(kTick % kCtaChunk == 0, "chunks tile a tick");
     const int npan = (Lb + P - 1) / P;
     float cut = PRUNE ? in.cut : EAP_FINF;   // the caller passes a CTA-uniform value
     abandoned = false;
@@ -104,16 +106,23 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     float4 pk_next = make_float4(0.f, 0.f, 0.f, 0.f);   // packed row constants, one row ahead (F::kPacked)
     bool lane_out = false;
 
+    // Where lane 0 reads its left input and lane 31 writes its output during
+    // a tick.  They change only at the tick barriers: the producer's live
+    // rows seen at the start of a tick cover every row read in it (a
+    // boundary row is written at least one tick before it is read, and a row
+    // past the producer's last live row is above the cut-off, so +inf stands
+    // in for it).
+    const float* lsrc = nullptr;   // shared-memory column of the left neighbour (panels > 0)
+    int lmask = 0, llo = 1, lhi = 0;
+    float* odst = nullptr;         // shared-memory column this panel feeds (null for the last panel)
+    int omask = 0;
     auto left_in = [&](int row) -> float {   // lane 0's left input at `row` of panel p
-        if (p == 0) return (row >= 1 && row <= bhi0) ? __ldg(in.bA + row - 1) : EAP_FINF;
-        const int q = p - 1;
-        if (row < pr0(q) || row > pr1(q) || row > sh.live_hi[q]) return EAP_FINF;
-        return (q % kCtaWarps == kCtaWarps - 1) ? wrapcol[row] : sh.ring[q % kCtaWarps][row % kRing];
+        if (row < llo || row > lhi) return EAP_FINF;
+        return p == 0 ? __ldg(in.bA + row - 1) : lsrc[row & lmask];
     };
     auto put_out = [&](int row, float x) {   // lane 31's output at `row` of panel p
-        if (p == npan - 1) return;
-        if (p % kCtaWarps == kCtaWarps - 1) wrapcol[row] = x;
-        else sh.ring[p % kCtaWarps][row % kRing] = x;
+        if (odst == nullptr) return;
+        odst[row & omask] = x;
         if (x <= cut) { my_live_hi = row; wrote_live = true; }
     };
 
@@ -157,11 +166,29 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
             const bool is_last = p == npan - 1;
             const int t_end = min((tick - S(p) + 1) * kTick, len);
             if (!pdead) {
-                for (; t < t_end; ++t) {
-                    const int row = r0 + t - lane;
-                    const bool act = row >= r0 && row <= r1;
+                if (p == 0) {
+                    llo = 1;
+                    lhi = bhi0;
+                } else {
+                    const int q = p - 1;
+                    const bool wrap = q % kCtaWarps == kCtaWarps - 1;
+                    lsrc = wrap ? wrapcol : sh.ring[q % kCtaWarps];
+                    lmask = wrap ? 0x7fffffff : kRing - 1;
+                    llo = pr0(q);
+                    lhi = min(pr1(q), sh.live_hi[q]);
+                }
+                const bool owrap = p % kCtaWarps == kCtaWarps - 1;
+                odst = is_last ? nullptr : (owrap ? wrapcol : sh.ring[p % kCtaWarps]);
+                omask = owrap ? 0x7fffffff : kRing - 1;
+                // One wavefront step; CHECK predicates the lanes outside the
+                // panel's rows (ramp at the start, rows past r1 at the end).
+                auto step = [&](int tt, auto check) {
+                    constexpr bool kCheck = decltype(check)::value;
+                    const int row = r0 + tt - lane;
+                    const bool act = kCheck ? (row >= r0 && row <= r1) : true;
+                    const float bv = (lane == 0 && act) ? left_in(row) : EAP_FINF;
                     float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1);
-                    if (lane == 0) x = act ? left_in(row) : EAP_FINF;
+                    if (lane == 0) x = bv;
                     if (act) {
                         typename F::Row rc;
                         if constexpr (kCtaPacked<F>) {
@@ -177,13 +204,27 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                         strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
                         dg = x;
                         if (lane == 31) put_out(row, v[W - 1]);
-                        if (is_last && lane == res_lane && row == La) {
-                            float res = EAP_FINF;
-#pragma unroll
-                            for (int u = 0; u < W; ++u) if (u == res_u) res = v[u];
-                            sh.result = res;   // M(La, Lb), recorded as soon as it exists
-                        }
                     }
+                };
+                // Unpredicated chunks of kCtaChunk steps while every lane's
+                // rows stay inside [r0, r1]; single predicated steps otherwise.
+                while (t < t_end) {
+                    if (t >= 31 && t + kCtaChunk <= t_end && t + kCtaChunk - 1 <= r1 - r0) {
+#pragma unroll
+                        for (int k = 0; k < kCtaChunk; ++k) step(t + k, BoolC<false>{});
+                        t += kCtaChunk;
+                    } else {
+                        step(t, BoolC<true>{});
+                        ++t;
+                    }
+                }
+                // M(La, Lb), once the lane holding it has computed row La (its
+                // strip is not touched again: later rows are past r1).
+                if (is_last && lane == res_lane && min(r1, r0 + t - 1 - lane) == La) {
+                    float res = EAP_FINF;
+#pragma unroll
+                    for (int u = 0; u < W; ++u) if (u == res_u) res = v[u];
+                    sh.result = res;
                 }
             } else {
                 t = t_end;

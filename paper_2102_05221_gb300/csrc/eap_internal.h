@@ -53,6 +53,7 @@ void tune_reset();
 void map_set(int kind, int cost, int bucket, int m);   // 0 untuned, 1 warp, 2 CTA
 int pick_w(int kind, int cost, int max_cols, int prune);
 int pick_cta(int kind, int cost, int max_rows, int max_cols, int prune);
+int pick_w_cta(int kind, int cost, int max_cols, int prune);
 int pick_group(int kind, int cost, int max_rows, int max_cols, int prune, int W);
 void pick_w_group(int kind, int cost, int max_rows, int max_cols, int prune, int* W, int* G);
 // Band mapping of the windowed DP: strip width and lanes per pair, or 0

@@ -563,7 +563,7 @@ extern "C" int eap_subseq(const eap_params* p, const float* ref, int64_t n, cons
             c.max_rows = m;
             c.max_cols = m;
             c.cta = eaph::pick_cta(p->kind, cost, m, m, kPmPruned);
-            if (c.cta) c.group = 0;
+            if (c.cta) { c.W = eaph::pick_w_cta(p->kind, cost, m, kPmPruned); c.group = 0; }
             c.stream = st;
             e |= p->kind == EAP_DTW ? eaph::launch_dp_dtw(c, false) : eaph::launch_dp_cdtw(c, false);
         }
