@@ -206,12 +206,53 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
                         if (lane == 31) put_out(row, v[W - 1]);
                     }
                 };
+                // A step of an unpredicated chunk: lane 0 takes its left input
+                // (loaded for the chunk, one row per lane) from lane k, and
+                // lane k keeps lane 31's output of the step.
+                auto chunk_step = [&](int tt, int k, float lb, float& ob) {
+                    const int row = r0 + tt - lane;
+                    float x = __shfl_up_sync(EAP_FULL, v[W - 1], 1);
+                    const float xb = __shfl_sync(EAP_FULL, lb, k);
+                    if (lane == 0) x = xb;
+                    typename F::Row rc;
+                    if constexpr (kCtaPacked<F>) {
+                        rc = F::unpack(pk_next);
+                        pk_next = __ldg(in.rp + row);   // row <= La: the entry past La is readable
+                    } else {
+                        const float s = s_next;
+                        s_next = __ldg(in.A + min(row, La - 1));
+                        rc = F::row(s, sp, kp, in.wt);
+                        sp = s;
+                    }
+                    shift_weights<F, W, WIN>(wr, in.wt, kp, row, c0, fd, w);
+                    strip_row<F, W, WIN>(v, cy, wr, cc, rc, dg, x, row - c0, w, kp);
+                    dg = x;
+                    const float o = __shfl_sync(EAP_FULL, v[W - 1], 31);
+                    if (lane == k) ob = o;
+                };
                 // Unpredicated chunks of kCtaChunk steps while every lane's
                 // rows stay inside [r0, r1]; single predicated steps otherwise.
+                // A chunk reads lane 0's left inputs and writes lane 31's
+                // outputs with one coalesced access each (lane j: step j).
                 while (t < t_end) {
                     if (t >= 31 && t + kCtaChunk <= t_end && t + kCtaChunk - 1 <= r1 - r0) {
+                        float lb = EAP_FINF, ob = 0.f;
+                        {
+                            const int brow = r0 + t + lane;   // lane 0's row at step t + lane
+                            if (lane < kCtaChunk && brow >= llo && brow <= lhi)
+                                lb = p == 0 ? __ldg(in.bA + brow - 1) : lsrc[brow & lmask];
+                        }
 #pragma unroll
-                        for (int k = 0; k < kCtaChunk; ++k) step(t + k, BoolC<false>{});
+                        for (int k = 0; k < kCtaChunk; ++k) chunk_step(t + k, k, lb, ob);
+                        if (odst != nullptr) {
+                            const int orow = r0 + t + lane - 31;   // lane 31's row at step t + lane
+                            if (lane < kCtaChunk) odst[orow & omask] = ob;
+                            const unsigned live = __ballot_sync(EAP_FULL, lane < kCtaChunk && ob <= cut);
+                            if (live != 0u && lane == 31) {
+                                my_live_hi = r0 + t + (31 - __clz(live)) - 31;
+                                wrote_live = true;
+                            }
+                        }
                         t += kCtaChunk;
                     } else {
                         step(t, BoolC<true>{});
