@@ -358,7 +358,7 @@ namespace eapd {
 // Persistent CTA-per-pair kernel (1-NN, all-pairs and explicit pairs as
 // dp_kernel); one pair per CTA at a time.
 template <class F, int W, bool PRUNE>
-__global__ void __launch_bounds__(kCtaThreads) cta_dp_kernel(const DPJob job, const KParams kp) {
+__global__ void __launch_bounds__(kCtaThreads, F::kCtaBlocks) cta_dp_kernel(const DPJob job, const KParams kp) {
     __shared__ CtaShared sh;
     extern __shared__ float wrapcol[];
     unsigned long long cells = 0, npairs = 0, nab = 0, nlb = 0;

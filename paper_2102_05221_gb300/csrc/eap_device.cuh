@@ -95,6 +95,10 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 // takes the fewest registers that do not spill).  With the group's cold state
 // in shared memory every distance's default is the fastest measured on
 // 1000 x 1000 x 512 (TWE: 88 registers, 34.8 ms; capped at 80, 35.2 ms).
+// Each functor's kCtaBlocks is the same for cta_dp_kernel (256 threads): 0
+// for every distance but MSM, which asks for 3 (80 registers at W = 8 instead
+// of 104, 3 CTAs per SM instead of 2: 1-NN at L = 8192, 66.2 -> 62.9 ms; TWE
+// capped the same way measured slower, 56.5 -> 58.6 ms).
 #ifndef EAP_MINB_DTW
 #define EAP_MINB_DTW 0
 #endif
@@ -157,6 +161,7 @@ struct FDtw {
     static constexpr bool kPacked = false;   // the row constant is s_i itself
     static constexpr bool kX2 = EAP_X2_DTW;
     static constexpr int kGroupBlocks = EAP_MINB_DTW;
+    static constexpr int kCtaBlocks = 0;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -209,6 +214,7 @@ struct FWdtw {
     static constexpr bool kPacked = false;
     static constexpr bool kX2 = EAP_X2_DTW;
     static constexpr int kGroupBlocks = EAP_MINB_WDTW;
+    static constexpr int kCtaBlocks = 0;
     struct Col { float t; };
     struct Row { float s; const float* wt; };
     __device__ static Col col(float t, float, const KParams&) { return {t}; }
@@ -265,6 +271,7 @@ struct FErp {
     static constexpr bool kPacked = true;    // row constants precomputed per point (rowpack_kernel)
     static constexpr bool kX2 = EAP_X2;
     static constexpr int kGroupBlocks = EAP_MINB_ERP;
+    static constexpr int kCtaBlocks = 0;
     struct Col { float t, ct; };
     struct Row { float2 s2, cs2; };          // (s_i, s_i), (cost(s_i, g), cost(s_i, g))
     __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.cs2.x, r.cs2.y); }
@@ -340,6 +347,7 @@ struct FMsm {
     static constexpr bool kPacked = true;
     static constexpr bool kX2 = EAP_X2;
     static constexpr int kGroupBlocks = EAP_MINB_MSM;
+    static constexpr int kCtaBlocks = 3;
     struct Col { float t, ig, ag; };   // g = t_{j-1} - t_j: ig = 1/g (0 if g = 0), ag = |g|
     struct Row { float2 s2; float ie, ae; };   // s2 = (s_i, s_i); e = s_{i-1} - s_i: ie = 1/e (0 if e = 0), ae = |e|
     __device__ static float4 pack(const Row& r) { return make_float4(r.s2.x, r.s2.y, r.ie, r.ae); }
@@ -420,6 +428,7 @@ struct FTwe {
     static constexpr bool kPacked = true;
     static constexpr bool kX2 = EAP_X2_TWE;
     static constexpr int kGroupBlocks = EAP_MINB_TWE;
+    static constexpr int kCtaBlocks = 0;
     struct Col { float t, tprev, gb; };   // gb = cost(t_j, t_{j-1}) + nu + lambda
     struct Row { float s, sprev; float2 ga2; };   // ga2 = (ga, ga), ga = cost(s_i, s_{i-1}) + nu + lambda
     __device__ static float4 pack(const Row& r) { return make_float4(r.s, r.sprev, r.ga2.x, r.ga2.y); }
