@@ -310,7 +310,7 @@ def main():
     ap.add_argument("--mode", default="per-distance", choices=["per-distance", "batch"],
                     help="per-distance: one eap_nn1 call per distance; batch: all six in one eap_nn1_batch launch")
     ap.add_argument("--workload", default="nn1_512",
-                    choices=["nn1_512", "unpruned_512", "modes_512", "subseq", "allpairs_4096", "uneven_64",
+                    choices=["nn1_512", "unpruned_512", "modes_512", "subseq", "allpairs_4096", "nn1_8192", "uneven_64",
                              "serving", "lb_cascade"],
                     help="nn1_512 is the benchmark; the others measure the remaining workloads")
     args = ap.parse_args()
@@ -816,6 +816,36 @@ def workload_allpairs_4096(args):
             "config": {"workload": "allpairs_256_L4096", "n": n, "length": int(x.shape[1])}, "per_distance": res}
 
 
+def workload_nn1_8192(args):
+    """1-NN of 16 queries against 200 candidates of 8192 points, EAPruned, for
+    DTW, MSM and TWE (unwindowed: one CTA per pair at this length; WDTW's
+    weights underflow float32 there at the benchmark's g): whole-call time,
+    DP time and the DP's fraction of the ALU roofline on computed cells."""
+    import torch
+
+    from paper_2102_05221_gb300 import eap, synth
+    ds = synth.workload_nn1_8192()
+    R = eap.SeriesSet.from_matrix(ds.train)
+    Q = eap.SeriesSet.from_matrix(ds.test)
+    props = torch.cuda.get_device_properties(0)
+    res = {}
+    for k in ("dtw", "msm", "twe"):
+        p = eap.params(k, **KIND_PARAMS[k])
+        eap.eap_nn1(p, Q, R)
+        t = _sync_time(lambda: eap.eap_nn1(p, Q, R), reps=max(1, args.steps))
+        _, _, st = eap.eap_nn1(p, Q, R, with_stats=True)
+        res[k] = {"ms_per_call": t, "dp_ms": st["dp_ms"], "queries_per_s": Q.count / (t / 1e3),
+                  "computed_over_effective": st["cells_computed"] / st["cells_effective"],
+                  "alu_frac": st["cells_computed"] / (st["dp_ms"] / 1e3) * OPS_PER_CELL[k] / _alu_peak(props)}
+    tot = sum(r["ms_per_call"] for r in res.values())
+    return {"metric": "1-NN queries/s, long series (DTW, MSM, TWE; EAPruned; 200 train x 16 test, L=8192)",
+            "value": len(res) * Q.count / (tot / 1e3), "unit": "queries/s", "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "nn1_long_200x16_L8192", "n_train": R.count, "n_test": Q.count, "length": 8192,
+                       "mapping": "one CTA (8 warps) per pair, the default from 6144 points"},
+            "per_distance": res}
+
+
 def _uneven_tasks(eap, synth):
     ds = synth.workload_uneven()
     tasks, meta = [], []
@@ -1000,7 +1030,7 @@ def run_other_workload(args):
     from paper_2102_05221_gb300 import eap
     eap.load()
     fn = {"unpruned_512": workload_unpruned_512, "modes_512": workload_modes_512, "subseq": workload_subseq,
-          "allpairs_4096": workload_allpairs_4096,
+          "allpairs_4096": workload_allpairs_4096, "nn1_8192": workload_nn1_8192,
           "uneven_64": workload_uneven_64, "serving": workload_serving, "lb_cascade": workload_lb_cascade}[args.workload]
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()

@@ -191,6 +191,12 @@ def workload_nn1_512(n_train: int = 1000, n_test: int = 1000, seed_offset: int =
     return make_dataset(n_train, n_test, 512, 10, seed_for(2, seed_offset))
 
 
+def workload_nn1_8192(n_train: int = 200, n_test: int = 16, seed_offset: int = 0) -> Dataset:
+    """200 train x 16 test, length 8192 (the longest serving set), 10 classes:
+    1-NN over long series, which run one CTA per pair."""
+    return make_dataset(n_train, n_test, 8192, 10, seed_for(6, seed_offset))
+
+
 def workload_allpairs_4096(n: int = 256, length: int = 4096, seed_offset: int = 0) -> np.ndarray:
     """n random walks (no template) of the given length, for all-pairs matrices."""
     rng = _rng(seed_for(3, seed_offset))
