@@ -33,7 +33,12 @@ namespace eapd {
 
 constexpr int kCtaWarps = 8;
 constexpr int kCtaThreads = 32 * kCtaWarps;
-constexpr int kTick = 64;          // wavefront steps per tick
+// Wavefront steps per tick.  128: unwindowed (the only form this kernel
+// runs), a panel's producer leads its consumer by lag = 2 ticks plus 31 rows
+// at most, inside the 512-row ring; against 64, half the barriers and votes
+// (1-NN at L = 8192: DTW 12.2 -> 11.3 ms, MSM 63.0 -> 61.3 ms, TWE 56.4 ->
+// 54.9 ms; 32 is slower still).
+constexpr int kTick = 128;
 constexpr int kRing = 512;         // rows per in-round link
 constexpr int kCtaMaxPanels = 512;
 
@@ -58,7 +63,7 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int La = in.La, Lb = in.Lb, w = in.w;
     constexpr int P = 32 * W;
-    constexpr int kCtaChunk = kTick / W;   // unrolled steps per chunk (16 at W = 4, 8 at W = 8)
+    constexpr int kCtaChunk = 64 / W;      // unrolled steps per chunk (16 at W = 4, 8 at W = 8)
     static_assert(kTick % kCtaChunk == 0, "chunks tile a tick");
     const int npan = (Lb + P - 1) / P;
     float cut = PRUNE ? in.cut : EAP_FINF;   // the caller passes a CTA-uniform value
@@ -69,6 +74,12 @@ __device__ float cta_pair(const PairIn& in, CtaShared& sh, float* __restrict__ w
     auto plen = [&](int p) { return max(0, pr1(p) - pr0(p) + 1) + 31; };   // sweep steps of panel p
     const int dr0 = WIN ? min(P, La) : 0;
     const int lag = 1 + (dr0 + 31 + kTick - 1) / kTick;
+    // The ring holds a round's boundary rows between producer and consumer:
+    // the lead lag * kTick + 31 must stay below kRing.  Unwindowed, dr0 = 0
+    // and lag = 2; a window would shift every panel's rows by a panel width
+    // (the window keeps the warp or band mappings).
+    static_assert(!WIN, "the CTA mapping runs unwindowed series only");
+    static_assert(2 * kTick + 31 < kRing, "ring too short for the tick");
     int len_max = 0;
     for (int q = 0; q < npan; ++q) len_max = max(len_max, plen(q));
     const int T_round = max((len_max + kTick - 1) / kTick + lag, kCtaWarps * lag);
