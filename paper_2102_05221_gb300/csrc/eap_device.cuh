@@ -468,34 +468,72 @@ struct FTwe {
     }
     __device__ static float carry_first(const Row& r, const Col& c0) { return pcost<COST>(r.sprev, c0.tprev); }
     __device__ static float carry_init(float sprev, const Col& c) { return pcost<COST>(sprev, c.t); }
-    // One row of a strip, cell_c() for every cell with the same operations;
-    // s_i - t_j and the vertical candidate run on neighbouring cells in pairs.
+    // One row of a strip, cell_c() for every cell with the same operations:
+    // s_i - t_j and the vertical candidate run on neighbouring cells in
+    // pairs.  Up to W = 5 (the 16-lane groups) every term that does not
+    // depend on the cell to the left comes first, then the left-to-right
+    // chain (horizontal candidate and minimum): 35.1 -> 34.7 ms on
+    // 1000 x 1000 x 512.  At W = 8 (the CTA mapping) the cells are finished
+    // one by one, which measured faster there (L = 8192: 54.8 against
+    // 56.9 ms).  Pairing the match cost and the diagonal candidate as well
+    // measured slower (96 registers, register moves: 36.7 ms).
     template <int W, bool WIN>
     __device__ static void strip(float (&v)[W], float (&cy)[W], const float (&wr)[W], const Col (&cc)[W],
                                  const Row& rc, float dg, float lf, const KParams&) {
         static_assert(!WIN, "TWE has no window");
         auto pc = [](float d) { return COST == 0 ? __fmul_rn(d, d) : fabsf(d); };
         float cin = carry_first(rc, cc[0]);
-        auto finish = [&](int u, float dgu, float c1, float b) {
-            const float gm = __fadd_rn(__fadd_rn(c1, cin), wr[u]);
-            cin = cy[u];
-            cy[u] = c1;
-            const float nv = min3f(__fadd_rn(dgu, gm), b, __fadd_rn(lf, cc[u].gb));
-            v[u] = nv;
-            lf = nv;
-        };
+        if constexpr (W > 5) {
+            auto finish = [&](int u, float dgu, float c1, float bu) {
+                const float gm = __fadd_rn(__fadd_rn(c1, cin), wr[u]);
+                cin = cy[u];
+                cy[u] = c1;
+                const float nv = min3f(__fadd_rn(dgu, gm), bu, __fadd_rn(lf, cc[u].gb));
+                v[u] = nv;
+                lf = nv;
+            };
+#pragma unroll
+            for (int u = 0; u + 1 < W; u += 2) {
+                const float2 d2 = sub2_rn(make_float2(rc.s, rc.s), make_float2(cc[u].t, cc[u + 1].t));
+                const float2 b2 = __fadd2_rn(make_float2(v[u], v[u + 1]), rc.ga2);
+                const float dg0 = dg, dg1 = v[u];
+                dg = v[u + 1];
+                finish(u, dg0, pc(d2.x), b2.x);
+                finish(u + 1, dg1, pc(d2.y), b2.y);
+            }
+            if constexpr (W % 2 == 1) {
+                constexpr int u = W - 1;
+                finish(u, dg, pc(__fsub_rn(rc.s, cc[u].t)), __fadd_rn(v[u], rc.ga2.x));
+            }
+            return;
+        }
+        float a[W], b[W];
 #pragma unroll
         for (int u = 0; u + 1 < W; u += 2) {
             const float2 d2 = sub2_rn(make_float2(rc.s, rc.s), make_float2(cc[u].t, cc[u + 1].t));
+            const float c1a = pc(d2.x), c1b = pc(d2.y);
+            const float cina = cin, cinb = cy[u];   // cost(s_{i-1}, t_{j-1}) of both cells
+            cin = cy[u + 1];
+            cy[u] = c1a;
+            cy[u + 1] = c1b;
+            a[u] = __fadd_rn(u == 0 ? dg : v[u - 1], __fadd_rn(__fadd_rn(c1a, cina), wr[u]));
+            a[u + 1] = __fadd_rn(v[u], __fadd_rn(__fadd_rn(c1b, cinb), wr[u + 1]));
             const float2 b2 = __fadd2_rn(make_float2(v[u], v[u + 1]), rc.ga2);
-            const float dg0 = dg, dg1 = v[u];
-            dg = v[u + 1];
-            finish(u, dg0, pc(d2.x), b2.x);
-            finish(u + 1, dg1, pc(d2.y), b2.y);
+            b[u] = b2.x;
+            b[u + 1] = b2.y;
         }
         if constexpr (W % 2 == 1) {
             constexpr int u = W - 1;
-            finish(u, dg, pc(__fsub_rn(rc.s, cc[u].t)), __fadd_rn(v[u], rc.ga2.x));
+            const float c1 = pc(__fsub_rn(rc.s, cc[u].t));
+            a[u] = __fadd_rn(u == 0 ? dg : v[u - 1], __fadd_rn(__fadd_rn(c1, cin), wr[u]));
+            b[u] = __fadd_rn(v[u], rc.ga2.x);
+            cy[u] = c1;
+        }
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            const float nv = min3f(a[u], b[u], __fadd_rn(lf, cc[u].gb));
+            v[u] = nv;
+            lf = nv;
         }
     }
 };
