@@ -567,14 +567,24 @@ int length_bucket(int len) {
     return b;
 }
 
-// Warp-per-pair or CTA-per-pair: CTA for unwindowed series of 2048 and more
-// (EAP_MAP=warp|cta overrides).  Windowed bands keep the warp mapping: their
-// panels' rows shift by a panel width, which starves the CTA pipeline.
+// Warp-per-pair or CTA-per-pair for unwindowed series (EAP_MAP=warp|cta and
+// the autotuner's map override the defaults).  CTA from 6144 points, where a
+// warp's boundary column no longer fits beside enough warps.  For a 1-NN
+// search of at most 32 queries (n_queries; 0 = not a 1-NN search) also from
+// 2048 points for DTW and MSM: with few queries the warp mapping runs most of
+// a query's candidates at once, before any of them has tightened the
+// query's cut-off, while the CTA mapping runs about three pairs per SM.
+// Measured, 16 queries x 300-600 candidates: DTW 4.8 -> 2.5 ms at L = 2048,
+// 10.1 -> 4.0 ms at 4096; MSM 14.3 -> 12.1 and 32.0 -> 21.2 ms.  With 128
+// queries the warp mapping is faster up to 4096 points (DTW 9.9 against
+// 15.6 ms at 2048), and TWE gains nothing consistent below 6144.  Windowed
+// bands keep the warp mapping: their panels' rows shift by a panel width,
+// which starves the CTA pipeline.
 int length_bucket(int len);
 std::mutex g_map_mu;
 int g_map[6][2][16] = {};   // [kind][cost][bucket] -> 0 untuned, 1 warp, 2 CTA (set by the autotuner)
 
-int choose_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
+int choose_cta(int kind, int cost, int max_rows, int max_cols, int prune, int n_queries = 0) {
     if (kind == EAP_CDTW || kind == EAP_ERP) return 0;
     if (prune == kPmEA) return 0;   // EABase runs on the warp mapping only
     const char* e = std::getenv("EAP_MAP");
@@ -585,7 +595,11 @@ int choose_cta(int kind, int cost, int max_rows, int max_cols, int prune) {
         const int m = g_map[kind][cost][length_bucket(std::max(max_rows, max_cols))];
         if (m) return m == 2 ? 1 : 0;
     }
-    return (max_rows >= 6144 && max_cols >= 6144) ? 1 : 0;
+    if (max_rows >= 6144 && max_cols >= 6144) return 1;
+    if (n_queries > 0 && n_queries <= 32 && prune == kPmPruned && (kind == EAP_DTW || kind == EAP_MSM) &&
+        max_rows >= 2048 && max_cols >= 2048)
+        return 1;
+    return 0;
 }
 
 int choose_w(int kind, int cost, int max_cols, int prune) {
@@ -948,7 +962,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.sms = sms;
     c.max_rows = mq;
     c.max_cols = mr;
-    c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune);
+    c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune, nq);
     choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w_cta(p->kind, cost, mr, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g, &c.band_exact);
@@ -1690,7 +1704,7 @@ int nn1_dp_launch(const eap_params* p, const eap_series_set* qs, const eap_serie
     c.sms = sms;
     c.max_rows = max_rows;
     c.max_cols = max_cols;
-    c.cta = choose_cta(p->kind, cost, max_rows, max_cols, c.prune);
+    c.cta = choose_cta(p->kind, cost, max_rows, max_cols, c.prune, qs->count);
     choose_w_group(p->kind, cost, max_rows, max_cols, c.prune, &c.W, &c.group);
     if (c.cta) { c.W = choose_w_cta(p->kind, cost, max_cols, c.prune); c.group = 0; }
     choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(max_rows, max_cols),

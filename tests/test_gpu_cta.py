@@ -14,20 +14,26 @@ pytestmark = pytest.mark.gpu
 UNWINDOWED = ["dtw", "wdtw", "msm", "twe"]
 
 
-def _with_map(mapping, fn):
-    old = os.environ.get("EAP_MAP")
-    os.environ["EAP_MAP"] = mapping
+def _with_map(mapping, fn, **env):
+    env = {"EAP_MAP": mapping, **env}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         return fn()
     finally:
-        if old is None:
-            del os.environ["EAP_MAP"]
-        else:
-            os.environ["EAP_MAP"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
 
 
+@pytest.mark.parametrize("W", ["4", "8"])
 @pytest.mark.parametrize("kind", UNWINDOWED)
-def test_cta_pairs_match_warp_mapping_and_oracle(kind):
+def test_cta_pairs_match_warp_mapping_and_oracle(kind, W):
+    # Both strip widths of the CTA kernel (8 by default, 4 when asked for):
+    # every cell is the same operations at any width, so the results are
+    # bit-identical to the warp mapping's.
     from paper_2102_05221_gb300 import eap
     rng = np.random.default_rng(21)
     la = [1, 5, 130, 700, 1030, 2500, 1500, 64]
@@ -40,7 +46,7 @@ def test_cta_pairs_match_warp_mapping_and_oracle(kind):
     kw = WORKLOAD_PARAMS[kind]
     p0 = gpu_params(eap, kind, prune=0, **kw)
     base_w = _with_map("warp", lambda: eap.eap_pairs(p0, A, B, ia, ib).cpu().numpy())
-    base_c = _with_map("cta", lambda: eap.eap_pairs(p0, A, B, ia, ib).cpu().numpy())
+    base_c = _with_map("cta", lambda: eap.eap_pairs(p0, A, B, ia, ib).cpu().numpy(), EAP_W=W)
     assert np.array_equal(base_w, base_c), (kind, base_w, base_c)
     for k in range(len(la)):
         ref = O.distance(oracle_params(kind, **kw), Ap.series(k), Bp.series(k))
@@ -50,7 +56,7 @@ def test_cta_pairs_match_warp_mapping_and_oracle(kind):
     for cut in (base_w, np.where(fin, np.nextafter(base_w, np.float32(0)), base_w).astype(np.float32),
                 np.zeros_like(base_w), (base_w * np.float32(0.7)).astype(np.float32),
                 (base_w * np.float32(1.2)).astype(np.float32)):
-        got = _with_map("cta", lambda: eap.eap_pairs(p1, A, B, ia, ib, cut).cpu().numpy())
+        got = _with_map("cta", lambda: eap.eap_pairs(p1, A, B, ia, ib, cut).cpu().numpy(), EAP_W=W)
         want = np.where(base_w <= cut, base_w, np.float32(np.inf))
         assert np.array_equal(got, want), (kind, got, want)
 
