@@ -150,6 +150,34 @@ int eap_nn1_host(const eap_params* p,
                  const float* r_data, const int64_t* r_offsets, const int32_t* r_lengths, int32_t nr,
                  int32_t* out_idx, float* out_dist, eap_stats* opt_stats);
 
+/* Which kernel mapping, and which strip width, an eap_nn1 call with these
+ * parameters and sizes runs.  The paper has no counterpart (its search runs
+ * one pair at a time on one CPU thread); this reports the library's own
+ * choice.  Host only: it reads no device memory, launches nothing and works
+ * without a GPU.  The choice follows eap_nn1 exactly: distance and mode
+ * (p), number of queries, the shortest series of both sets, the longest
+ * query and the longest candidate, the EAP_MAP / EAP_W / EAP_G / EAP_BAND*
+ * environment overrides and the autotuner's table.
+ *   out->mapping        : EAP_PLAN_BAND (band coordinates, windowed CDTW/ERP),
+ *                         EAP_PLAN_GROUP (several pairs per warp over column
+ *                         panels), EAP_PLAN_WARP (a warp per pair),
+ *                         EAP_PLAN_CTA (8 warps per pair, long series).
+ *   out->strip_width    : cells a lane computes per row.
+ *   out->lanes_per_pair : 4, 8 or 16 (band, groups), 32 (warp), 256 (CTA).
+ *   out->band_exact     : 1 when a band launch covers exactly the 2w + 2
+ *                         positions of a band row, else 0.
+ * Returns EAP_EINVAL for invalid parameters, out == NULL, n_queries < 0,
+ * or lengths outside 1..8192 with min_len above either maximum. */
+typedef enum { EAP_PLAN_BAND = 1, EAP_PLAN_GROUP = 2, EAP_PLAN_WARP = 3, EAP_PLAN_CTA = 4 } eap_plan_mapping;
+typedef struct {
+    int32_t mapping;
+    int32_t strip_width;
+    int32_t lanes_per_pair;
+    int32_t band_exact;
+} eap_plan;
+int eap_nn1_plan(const eap_params* p, int32_t n_queries, int32_t min_len, int32_t max_query_len,
+                 int32_t max_ref_len, eap_plan* out);
+
 /* 1-NN against one shard of the candidates, as packed keys for the one
  * exchange step of candidate sharding (Alg. 1 over the union of the shards
  * is the per-query minimum of the shards' keys).  Same search as eap_nn1;

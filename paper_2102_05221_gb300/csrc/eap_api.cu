@@ -752,6 +752,18 @@ void choose_w_group(int kind, int cost, int max_rows, int max_cols, int prune, i
     }
 }
 
+// The kernel mapping of a 1-NN search (c.kp must be set): CTA per pair,
+// groups of 8 or 16 lanes, a warp per pair, or band coordinates for the
+// windowed distances, with their strip widths.  eap_nn1, the batched
+// per-task launch and eap_nn1_plan all take it from here.
+void nn1_mapping(int kind, int cost, int prune, bool own_cut, int n_queries, int max_rows, int max_cols,
+                 int min_len, eaph::LaunchCtx& c) {
+    c.cta = own_cut ? 0 : choose_cta(kind, cost, max_rows, max_cols, prune, n_queries);
+    choose_w_group(kind, cost, max_rows, max_cols, prune, &c.W, &c.group);
+    if (c.cta) { c.W = choose_w_cta(kind, cost, max_cols, prune); c.group = 0; }
+    choose_band(kind, prune, c.kp, min_len, std::max(max_rows, max_cols), &c.band, &c.band_g, &c.band_exact);
+}
+
 // DP launch bracketed by CUDA events on the call's stream when timing is asked.
 struct DpTimer {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -962,10 +974,7 @@ int nn1_core(const eap_params* p, const eap_series_set* qs, const eap_series_set
     c.sms = sms;
     c.max_rows = mq;
     c.max_cols = mr;
-    c.cta = own_cut ? 0 : choose_cta(p->kind, cost, mq, mr, c.prune, nq);
-    choose_w_group(p->kind, cost, mq, mr, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w_cta(p->kind, cost, mr, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(mq, mr), &c.band, &c.band_g, &c.band_exact);
+    nn1_mapping(p->kind, cost, c.prune, own_cut, nq, mq, mr, std::min(set_min_len(qs), set_min_len(rs)), c);
     c.stream = st;
     c.ub = d_ub;
     if (prune) {
@@ -1074,6 +1083,43 @@ int32_t eap_version(void) { return 1; }
 int eap_nn1(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs, int32_t* out_idx,
             float* out_dist, void* cuda_stream, eap_stats* opt_stats) {
     return nn1_impl(p, queries, refs, out_idx, out_dist, (cudaStream_t)cuda_stream, opt_stats, nullptr);
+}
+
+int eap_nn1_plan(const eap_params* p, int32_t n_queries, int32_t min_len, int32_t max_query_len,
+                 int32_t max_ref_len, eap_plan* out) {
+    if (!out || validate_params(p) != EAP_OK || n_queries < 0) return EAP_EINVAL;
+    if (min_len < 1 || max_query_len < min_len || max_ref_len < min_len || max_query_len > kMaxSeriesLen ||
+        max_ref_len > kMaxSeriesLen)
+        return EAP_EINVAL;
+    eaph::LaunchCtx c{};
+    c.kp = make_kparams(p);
+    const bool own_cut = p->prune == 3;
+    const int prune = own_cut ? kPmPruned : p->prune;
+    nn1_mapping(p->kind, resolve_cost(p), prune, own_cut, n_queries, max_query_len, max_ref_len, min_len, c);
+    // The order run_kind follows: band (windowed) or CTA (unwindowed) first,
+    // then groups (EAPruned and Base), then a warp per pair.
+    const bool windowed = p->kind == EAP_CDTW || p->kind == EAP_ERP;
+    eap_plan r{};
+    if (windowed && c.band) {
+        r.mapping = EAP_PLAN_BAND;
+        r.strip_width = c.band;
+        r.lanes_per_pair = c.band_g;
+        r.band_exact = c.band_exact;
+    } else if (!windowed && c.cta) {
+        r.mapping = EAP_PLAN_CTA;
+        r.strip_width = c.W >= 8 ? 8 : 4;
+        r.lanes_per_pair = eapd::kCtaThreads;
+    } else if (c.group && (prune == kPmPruned || prune == kPmBase)) {
+        r.mapping = EAP_PLAN_GROUP;
+        r.strip_width = c.W;
+        r.lanes_per_pair = c.group;
+    } else {
+        r.mapping = EAP_PLAN_WARP;
+        r.strip_width = c.W;
+        r.lanes_per_pair = 32;
+    }
+    *out = r;
+    return EAP_OK;
 }
 
 int eap_nn1_keys(const eap_params* p, const eap_series_set* queries, const eap_series_set* refs,
@@ -1704,11 +1750,8 @@ int nn1_dp_launch(const eap_params* p, const eap_series_set* qs, const eap_serie
     c.sms = sms;
     c.max_rows = max_rows;
     c.max_cols = max_cols;
-    c.cta = choose_cta(p->kind, cost, max_rows, max_cols, c.prune, qs->count);
-    choose_w_group(p->kind, cost, max_rows, max_cols, c.prune, &c.W, &c.group);
-    if (c.cta) { c.W = choose_w_cta(p->kind, cost, max_cols, c.prune); c.group = 0; }
-    choose_band(p->kind, c.prune, c.kp, std::min(set_min_len(qs), set_min_len(rs)), std::max(max_rows, max_cols),
-                &c.band, &c.band_g, &c.band_exact);
+    nn1_mapping(p->kind, cost, c.prune, false, qs->count, max_rows, max_cols,
+                std::min(set_min_len(qs), set_min_len(rs)), c);
     c.stream = st;
     return cuda_status(dispatch(c, false));
 }

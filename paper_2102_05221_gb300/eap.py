@@ -43,6 +43,14 @@ class eap_series_set(ctypes.Structure):
                 ("count", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
+class eap_plan(ctypes.Structure):
+    _fields_ = [("mapping", ctypes.c_int32), ("strip_width", ctypes.c_int32), ("lanes_per_pair", ctypes.c_int32),
+                ("band_exact", ctypes.c_int32)]
+
+
+PLAN_MAPPINGS = {1: "band", 2: "group", 3: "warp", 4: "cta"}
+
+
 class eap_stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_uint64), ("pairs_lb_pruned", ctypes.c_uint64),
                 ("pairs_abandoned", ctypes.c_uint64), ("cells_effective", ctypes.c_uint64),
@@ -92,6 +100,7 @@ def load(build_if_missing: bool = True):
                                      P(eap_stats)]
         lib.eap_keys_unpack.argtypes = [vp, i32, vp, vp, vp]
         lib.eap_lb_matrix.argtypes = [P(eap_params), P(eap_series_set), P(eap_series_set), i32, vp, vp]
+        lib.eap_nn1_plan.argtypes = [P(eap_params), i32, i32, i32, i32, P(eap_plan)]
         if hasattr(lib, "eap_serve_create"):
             lib.eap_serve_create.argtypes = [P(eap_serve_config), P(ctypes.c_int)]
             lib.eap_serve_create.restype = vp
@@ -233,6 +242,19 @@ def eap_lb_matrix(p: eap_params, queries: SeriesSet, refs: SeriesSet, two_way: b
                            ctypes.c_void_p(out.data_ptr() if out.numel() else 0), _stream_ptr(stream))
     _check(rc, "eap_lb_matrix")
     return out
+
+
+def eap_nn1_plan(p: eap_params, n_queries: int, min_len: int, max_query_len: int, max_ref_len: int) -> dict:
+    """The kernel mapping and strip width eap_nn1 runs for these sizes: a dict
+    with mapping ("band", "group", "warp" or "cta"), strip_width,
+    lanes_per_pair and band_exact.  Host only: needs no GPU."""
+    lib = load()
+    out = eap_plan()
+    rc = lib.eap_nn1_plan(ctypes.byref(p), int(n_queries), int(min_len), int(max_query_len), int(max_ref_len),
+                          ctypes.byref(out))
+    _check(rc, "eap_nn1_plan")
+    return {"mapping": PLAN_MAPPINGS[out.mapping], "strip_width": int(out.strip_width),
+            "lanes_per_pair": int(out.lanes_per_pair), "band_exact": bool(out.band_exact)}
 
 
 def eap_keys_unpack(keys, stream=None, out_idx=None, out_dist=None):
