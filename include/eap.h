@@ -167,7 +167,7 @@ int eap_nn1_host(const eap_params* p,
  *   out->band_exact     : 1 when a band launch covers exactly the 2w + 2
  *                         positions of a band row, else 0.
  * Returns EAP_EINVAL for invalid parameters, out == NULL, n_queries < 0,
- * a length outside 1..8192, or min_len above either maximum. */
+ * or lengths outside 1..8192 with min_len above either maximum. */
 typedef enum { EAP_PLAN_BAND = 1, EAP_PLAN_GROUP = 2, EAP_PLAN_WARP = 3, EAP_PLAN_CTA = 4 } eap_plan_mapping;
 typedef struct {
     int32_t mapping;
