@@ -154,8 +154,14 @@ __global__ void derivative_kernel(const float* __restrict__ data, const int64_t*
             float v = 0.f;
             if (L > 2) {
                 const int k = min(max(i, 1), L - 2);
-                const float xl = __ldg(x + k - 1), xc = __ldg(x + k), xr = __ldg(x + k + 1);
-                v = __fmul_rn(__fadd_rn(__fsub_rn(xc, xl), __fmul_rn(__fsub_rn(xr, xl), 0.5f)), 0.5f);
+                // In double, rounded to float once: the differences of float
+                // inputs and the halvings are exact in double, so each value is
+                // the float nearest the estimate.  (Rounded in float at every
+                // step, a distance much smaller than the derivative values --
+                // cancellation -- missed 1e-4 relative against the FP64
+                // oracle: 1.1e-4 for ERP between two 3-point series.)
+                const double xl = __ldg(x + k - 1), xc = __ldg(x + k), xr = __ldg(x + k + 1);
+                v = __double2float_rn(((xc - xl) + (xr - xl) * 0.5) * 0.5);
             }
             d[i] = v;
         }
