@@ -151,3 +151,29 @@ def test_derivative_flag_is_validated(eap):
     assert e.value.code == eap.EAP_EINVAL
     idx, dist = eap.eap_nn1(eap.params("dtw", derivative=1), Q, Q)
     assert idx.item() == 0 and dist.item() == 0.0 and not math.isnan(dist.item())
+
+
+def test_near_zero_distance_between_short_series(eap):
+    """ERP (squared cost) with derivative series, 7 queries against 39
+    candidates of 2 to 561 points (a seeded random configuration).  Query 2
+    and its nearest candidate have 3 points each, so both derivative series
+    are constant and the distance, 1.13e-5, is 3 (a - b)^2 with |a - b| far
+    below the values' size.  Per-step float rounding of the estimate missed
+    the 1e-4 relative tolerance here (1.1e-4); one rounding of an estimate
+    evaluated in double keeps it inside."""
+    from tests.test_gpu_random_configs import EDGE_LENGTHS, _config
+    seed = 50179
+    rng = np.random.default_rng(seed)
+    cfg = _config(rng)
+    assert cfg["kind"] == "erp" and cfg["gpu"]["derivative"] == 1
+    nq, nr = int(rng.integers(1, 12)), int(rng.integers(1, 40))
+    pool = EDGE_LENGTHS + list(rng.integers(1, 600, size=8))
+    qlen = [int(rng.choice(pool)) for _ in range(nq)]
+    rlen = [int(rng.choice(pool)) for _ in range(nr)]
+    Qp = synth.ragged_walks(nq, qlen, seed + 7, n_classes=3)
+    Rp = synth.ragged_walks(nr, rlen, seed + 11, n_classes=3)
+    Q, R = eap.SeriesSet.from_packed(Qp), eap.SeriesSet.from_packed(Rp)
+    idx, dist = eap.eap_nn1(eap.params("erp", **cfg["gpu"]), Q, R)
+    D = O.cross(O.make_params("erp", **cfg["orc"]), Qp, Rp)
+    assert qlen[2] == 3 and 0 < D[2].min() < 1e-4
+    check_nn(idx.cpu().numpy(), dist.cpu().numpy(), D)
